@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark: mixed-precision even-odd Wilson solve on a 32^3x64 lattice.
+
+One step = one solve of D x = b to a true FP64 residual ||b - D x|| / ||b|| <= 1e-10
+(random SU(3) links exp(i 0.3 H) seed 1, kappa = 0.12, antiperiodic in time,
+one complex Gaussian right-hand side seed 2), from b in HBM (canonical layout)
+to x in HBM: layout conversion in, even-odd preparation, inner BiCGStab in
+FP16 storage / FP32 arithmetic under FP64 defect correction, reconstruction,
+full-D true residual, layout conversion out.
+
+value = algorithmic bytes of every hopping-kernel launch of the timed steps
+(1536 / 768 / 392 B per output site for FP64 / FP32 / FP16, plus the xpay and
+clover operands) divided by the timed wall time: the dslash GB/s the whole
+solve sustains.  The roofline block reports the inner-precision hopping
+kernel alone (CUDA events around each launch, on its stream).
+
+--impl reference times the FP64 CPU oracle (the only reference: the paper
+ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_BENCH = (32, 32, 32, 64)
+KAPPA = 0.12
+TOL = 1e-10
+METRIC = "dslash GB/s (% of HBM peak); solve time to 1e-10 resid, mixed vs FP64"
+BYTES_F64 = 1536.0     # algorithmic bytes per eo-dslash output site, FP64 (8 links + in + out)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", default="f16", choices=["f16", "f32"])
+    ap.add_argument("--lattice", default=None, help="override lattice, e.g. 16,16,16,32")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BPP_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_sample(L, target_s=12.0):
+    """The FP64 oracle's D (Eq. 1, plain loops) on sampled sites of the lattice:
+    returns (GB/s of eo-dslash-equivalent algorithmic bytes, sites, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    V = L[0] * L[1] * L[2] * L[3]
+    U = synth.random_links(L, seed=1)
+    psi = synth.gaussian_spinor(L, seed=2)
+    rng = np.random.default_rng(0)
+    n = 4096
+    total_sites, total_t = 0, 0.0
+    while total_t < target_s:
+        sites = np.sort(rng.choice(V, size=min(n, V), replace=False))
+        t0 = time.perf_counter()
+        oracle.apply_D(U, psi, KAPPA, L, (1, 1, 1, -1), sites=sites)
+        dt = time.perf_counter() - t0
+        total_sites += len(sites)
+        total_t += dt
+        if dt < 0.5 * target_s:
+            n = min(V, n * 4)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return total_sites * BYTES_F64 / total_t / 1e9, total_sites, total_t, threads
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    L = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else L_BENCH
+    times, gbs = [], []
+    cores = None
+    for step in range(args.warmup + args.steps):
+        v, sites, secs, cores = cpu_oracle_sample(L, target_s=4.0)
+        if step >= args.warmup:
+            times.append(secs)
+            gbs.append(v)
+    value = statistics.mean(gbs)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "Wilson eo-dslash, 32^3x64, random SU(3) links eps=0.3 seed 1, kappa 0.12",
+                      "lattice": list(L)},
+           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                            "sample": "FP64 oracle D (Eq. 1, plain C loops, OpenMP) on random site samples of "
+                                      "the 32^3x64 lattice, ~4 s per step; bytes = 1536 B per output site"},
+           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2111_04457_b300 as bpp
+    import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else L_BENCH
+    V = L[0] * L[1] * L[2] * L[3]
+    inner = bpp.F16 if args.inner == "f16" else bpp.F32
+
+    U = synth.random_links(L, seed=1)
+    b_np = synth.gaussian_spinor(L, seed=2)
+    g = bpp.Gauge(torch.from_numpy(U).to(dev), L)
+    del U
+    b = torch.from_numpy(b_np).to(dev)
+    x = torch.empty_like(b)
+    opts = bpp.solve_opts(inner_prec=inner)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also runs the block-size autotuner on first use)
+    for _ in range(args.warmup):
+        _, st = bpp.solve(g, b, KAPPA, 0.0, TOL, opts, x=x)
+    torch.cuda.synchronize()
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    bpp.prof_enable(True)
+    for p in (0, 1, 2):
+        bpp.prof_read(p, reset=True)
+    bpp.launch_count(reset=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        _, st = bpp.solve(g, b, KAPPA, 0.0, TOL, opts, x=x)
+        stats.append(st[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    launches = bpp.launch_count()
+    bpp.prof_enable(False)
+    prof = {p: bpp.prof_read(p, reset=True) for p in (0, 1, 2)}
+    clk = clocks.stop()
+    ms = allreduce_max(ms_local, world, dev)
+    hop_bytes = sum(v[2] for v in prof.values())
+    hop_bytes_all = allreduce_sum(hop_bytes, world, dev)
+    value = hop_bytes_all / (ms / 1000.0) / 1e9
+    true_res = max(s["true_resid"] for s in stats)
+
+    # roofline of the dominant kernel (inner-precision hopping term)
+    n_in, ms_in, by_in = prof[inner]
+    achieved = by_in / (ms_in / 1000.0) / 1e9 if ms_in > 0 else None
+    peak, peak_kind = measured_peaks()
+    n64, ms64, by64 = prof[0]
+
+    # e2e: host pinned b -> solve (library copies in and out) -> host x
+    b_host = torch.from_numpy(b_np).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    for _ in range(1):
+        bpp.solve(g, b_host, KAPPA, 0.0, TOL, opts, x=x_host)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        bpp.solve(g, b_host, KAPPA, 0.0, TOL, opts, x=x_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = allreduce_max(e0.elapsed_time(e1), world, dev)
+    e2e_value = hop_bytes_all / (e2e_ms / 1000.0) / 1e9
+
+    # plain FP64 solve on the same GPU (comparison of the metric's second half)
+    fp64_ms = None
+    if not args.no_fp64:
+        o64 = bpp.solve_opts(inner_prec=bpp.F64)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, o64, x=x)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, st64 = bpp.solve(g, b, KAPPA, 0.0, TOL, o64, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1)
+    f32_ms = None
+    if inner != bpp.F32:
+        o32 = bpp.solve_opts(inner_prec=bpp.F32)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, o32, x=x)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, o32, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f32_ms = e0.elapsed_time(e1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sites, secs, cores = cpu_oracle_sample(L, target_s=12.0)
+        cpu = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle D (Eq. 1, plain C loops, OpenMP) on {sites} random sites of the "
+                         f"{L[0]}x{L[1]}x{L[2]}x{L[3]} lattice in {secs:.1f} s; 1536 B per output site"}
+
+    if rank != 0:
+        return
+    ms_step = ms / args.steps
+    inner_name = "f16-storage/f32" if inner == bpp.F16 else "f32"
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"{inner_name} inner, f64 outer", "data": "synthetic",
+        "config": {"workload": f"Wilson eo-BiCGStab solve, {'x'.join(map(str, L))}, kappa {KAPPA}, 1 Gaussian RHS, "
+                               f"{inner_name} inner + FP64 defect correction to true resid {TOL}",
+                   "lattice": list(L), "kappa": KAPPA, "tol": TOL, "rhs": 1,
+                   "l2": "inputs larger than L2 (links 1.2 GB FP64 / 0.6 GB FP32 / 0.3 GB FP16); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "solve_ms": ms_step,
+        "solve_ms_fp64": fp64_ms,
+        "solve_ms_f32_inner": f32_ms,
+        "speedup_vs_fp64": (fp64_ms / ms_step) if fp64_ms else None,
+        "true_resid": true_res,
+        "inner_iters": stats[-1]["inner_iters"], "outer_iters": stats[-1]["outer_iters"],
+        "hop_launches": {str(p): prof[p][0] for p in prof},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": V * 12 * 16,
+                "d2h_bytes_per_step": V * 12 * 16, "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": f"k_hop<{inner_name}> (even-odd hopping term, all fused epilogues)",
+                     "peak_kind": peak_kind, "launches": n_in, "avg_us": 1000 * ms_in / max(n_in, 1),
+                     "fp64_hop_gbs": (by64 / (ms64 / 1000.0) / 1e9) if ms64 > 0 else None},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

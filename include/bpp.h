@@ -1,0 +1,225 @@
+/*
+ * bpp.h -- C ABI of the B300 Wilson / Wilson-clover fermion-matrix library.
+ *
+ * The library applies the fermion matrix of Eq. (1) of "General purpose lattice
+ * QCD code set Bridge++ 2.0 for high performance computing" (arXiv:2111.04457,
+ * Sec. 3):
+ *
+ *   D_{x,y} = [1 + F(x)] delta_{x,y}
+ *             - kappa sum_mu [ (1 - gamma_mu) U_mu(x) delta_{x+mu,y}
+ *                            + (1 + gamma_mu) U_mu^dag(x-mu) delta_{x-mu,y} ]
+ *
+ * and solves D x = b (the linear problem Sec. 2 names as the main bottleneck)
+ * with the operator modes D / Ddag of Fig. 1 and float / double fields
+ * (Sec. 2, the AField<double>/AField<float> pair).  Work runs as CUDA kernels
+ * for sm_103a on one GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *   - Euclidean Hermitian gamma matrices in the chiral basis:
+ *       gamma_k = [[0, i sigma_k], [-i sigma_k, 0]] (k = 1, 2, 3),
+ *       gamma_4 = [[0, 1], [1, 0]], gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(-1,-1,1,1).
+ *   - Directions mu = 0..3 are x1..x4; the site index is
+ *       s = x1 + L1*(x2 + L2*(x3 + L3*x4));  parity (x1+x2+x3+x4) mod 2, even = 0.
+ *   - Boundary: a hop across the lattice boundary in direction mu is multiplied
+ *     by bc[mu] (+1 periodic, -1 antiperiodic); links themselves are periodic.
+ *   - Clover term: F = i kappa c_SW sum_{mu<nu} sigma_{mu nu} Fhat_{mu nu},
+ *     sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], Fhat = (Q - Q^dag)/8 from the
+ *     four-plaquette clover leaf Q.
+ *   - Canonical spinor layout: complex [nrhs][V][4][3] (spin, then colour),
+ *     lexicographic sites.  Half-lattice ("even-odd") fields hold the Vh = V/2
+ *     sites of one parity in lexicographic order.  L1 must be even.
+ *   - Canonical link layout: complex128 [4][V][3][3], row-major U_mu(x)[a][b].
+ *   - The complex element type of a canonical field is complex128 for BPP_F64
+ *     and complex64 for BPP_F32 and BPP_F16 (FP16 is a storage format: the
+ *     library converts at the boundary and computes in FP32).
+ *
+ * Errors: every function returns an int status, 0 = BPP_OK, < 0 an error code
+ * below.  No C++ exception crosses the ABI.  bpp_last_error() copies the
+ * message of the calling thread's last failure.  Calls are asynchronous on the
+ * given stream unless documented otherwise; a NULL stream is the legacy default
+ * stream.  The library never frees or keeps caller memory.
+ */
+#ifndef BPP_H_
+#define BPP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* bpp_stream; /* the same type as cudaStream_t */
+
+enum {
+    BPP_OK = 0,
+    BPP_ERR_INVALID_ARG = -1,   /* bad pointer, size, parity, precision or lattice */
+    BPP_ERR_UNSUPPORTED = -2,   /* valid request the library does not implement */
+    BPP_ERR_CUDA = -3,          /* a CUDA runtime call failed; see bpp_last_error */
+    BPP_ERR_OOM = -4,           /* device allocation failed */
+    BPP_ERR_NOT_CONVERGED = -5, /* solver hit max iterations or broke down; x is the best iterate */
+    BPP_ERR_NONFINITE = -6,     /* NaN or Inf met in an input or a residual */
+    BPP_ERR_TIMEOUT = -7        /* a bounded device-side wait ran out */
+};
+
+typedef enum { BPP_F64 = 0, BPP_F32 = 1, BPP_F16 = 2 } bpp_prec;
+typedef enum { BPP_EVEN = 0, BPP_ODD = 1, BPP_FULL = 2 } bpp_parity;
+typedef enum { BPP_BICGSTAB = 0, BPP_CGNR = 1 } bpp_solver;
+
+/* Lattice extents L[mu] (L[0] even, every L[mu] >= 2) and boundary signs bc[mu]
+ * in {+1, -1}; the paper's workloads use bc = {1, 1, 1, -1}. */
+typedef struct {
+    int L[4];
+    int bc[4];
+} bpp_lattice;
+
+/* Opaque gauge handle: owns device copies of the links in the internal
+ * even-odd structure-of-arrays layout in all three precisions, plus the clover
+ * term and its inverse once bpp_clover_build() ran. */
+typedef struct bpp_gauge_s* bpp_gauge;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int bpp_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to n bytes); returns the status code of that error (BPP_OK if none). */
+int bpp_last_error(char* buf, size_t n);
+
+/* Gauge field U_mu(x) of Eq. (1) (Sec. 2: "link variable U_mu(x) in SU(3)").
+ * U_lex: complex128 [4][V][3][3] in device or host memory (detected); copied,
+ * the caller keeps ownership.  Synchronises `stream` before returning.
+ * Errors: INVALID_ARG (NULL pointer, odd L[0], L[mu] < 2, bc not +-1),
+ * OOM, CUDA. */
+int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream stream, bpp_gauge* out);
+
+/* Frees the gauge handle and everything it owns (synchronises the device). */
+int bpp_gauge_destroy(bpp_gauge g);
+
+/* Builds the clover term F(x) of Eq. (1) ("a 12x12 Hermitian matrix made of
+ * the link variables", Sec. 3) as two 6x6 Hermitian chiral blocks per site,
+ * A = 1 + F and A^{-1} (per block, FP64 Gauss-Jordan), cached on the handle for
+ * this (kappa, c_SW).  Must be called before any clover use (csw != 0).
+ * Errors: INVALID_ARG, NONFINITE (a block is singular), OOM, CUDA. */
+int bpp_clover_build(bpp_gauge g, double kappa, double csw, bpp_stream stream);
+
+/* Hopping term of Eq. (1) between parities, or the full Wilson matrix.
+ *   parity BPP_EVEN/BPP_ODD: out_p = -kappa H_{p,pbar} psi_pbar, where psi is
+ *     the half field of the opposite parity and out the half field of parity p,
+ *     both canonical [nrhs][Vh][4][3].  The clover term is not applied.
+ *   parity BPP_FULL: out = D_W psi = psi - kappa H psi on the full lattice
+ *     (F = 0), canonical [nrhs][V][4][3].
+ * psi, out: device memory, caller-owned, of element type complex<prec>; out
+ * must not alias psi.  The arithmetic is done in `prec` (BPP_F16: FP16 storage
+ * of fields and links, FP32 arithmetic).
+ * Errors: INVALID_ARG (NULL, nrhs < 1, bad parity/prec), OOM, CUDA. */
+int bpp_dslash(bpp_gauge U, const void* psi, void* out, double kappa, int parity, int prec,
+               int nrhs, bpp_stream stream);
+
+/* Clover term of Eq. (1) on one parity: out = (1 + F) in, or (1 + F)^{-1} in
+ * when inverse != 0.  in/out: device, canonical half fields [nrhs][Vh][4][3]
+ * of complex<prec>; parity BPP_EVEN or BPP_ODD.  Requires bpp_clover_build.
+ * Errors: INVALID_ARG, UNSUPPORTED (no clover built), OOM, CUDA. */
+int bpp_clover_apply(bpp_gauge U, const void* in, void* out, int parity, int inverse, int prec,
+                     int nrhs, bpp_stream stream);
+
+/* Even-odd preconditioned operator on the even half lattice,
+ *   Mhat = A_ee - kappa^2 H_eo A_oo^{-1} H_oe   (A = 1 + F, A = 1 when csw = 0),
+ * or its adjoint Mhat^dag = gamma5 Mhat gamma5 when dagger != 0.  csw != 0
+ * requires bpp_clover_build with the same kappa and csw.  in/out: device,
+ * canonical even half fields [nrhs][Vh][4][3] of complex<prec>.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int bpp_schur_apply(bpp_gauge U, const void* in, void* out, double kappa, double csw, int dagger,
+                    int prec, int nrhs, bpp_stream stream);
+
+/* The full matrix D of Eq. (1) (clover included when csw != 0), or D^dag when
+ * dagger != 0, in FP64 on canonical full fields complex128 [nrhs][V][4][3],
+ * device memory.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int bpp_dirac_apply(bpp_gauge U, const void* in, void* out, double kappa, double csw, int dagger,
+                    int nrhs, bpp_stream stream);
+
+/* Solver options.  The outer loop is FP64 defect correction (Sec. 2, Fig. 1:
+ * the double/float mixed-precision propagator solver; Sec. 3: float plays the
+ * main role in multi-precision solvers): r = bhat - Mhat x in FP64, an inner
+ * Krylov solve of Mhat e = r/|r| in inner_prec to relative tolerance
+ * inner_tol, x += |r| e.  inner_prec = BPP_F64 is the plain FP64 solve. */
+typedef struct {
+    int solver;       /* bpp_solver: BPP_BICGSTAB or BPP_CGNR on the Schur system */
+    int inner_prec;   /* bpp_prec of the inner Krylov solve */
+    double inner_tol; /* relative residual reduction per inner solve (ignored for F64) */
+    int max_inner;    /* iteration cap of one inner solve */
+    int max_outer;    /* cap on defect-correction steps */
+    int use_x0;       /* nonzero: x holds the initial guess on entry */
+    int dagger;       /* nonzero: solve D^dag x = b (through gamma5-hermiticity) */
+    int check_every;  /* inner iterations between host-side convergence checks */
+} bpp_solve_opts;
+
+/* Per right-hand side statistics of a solve. */
+typedef struct {
+    int outer_iters;    /* defect-correction steps */
+    int inner_iters;    /* total inner Krylov iterations */
+    int converged;      /* 1 if true_resid <= tol */
+    int status;         /* BPP_OK or the per-RHS error code */
+    double true_resid;  /* ||b - D x|| / ||b||, full FP64 D recomputed from scratch */
+    double seconds;     /* wall time of the whole call (same for every RHS) */
+} bpp_solve_stats;
+
+/* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 1e-5,
+ * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 16. */
+void bpp_solve_opts_default(bpp_solve_opts* opts);
+
+/* Solves D x = b (or D^dag x = b) for nrhs right-hand sides sharing the gauge
+ * field, to a true FP64 residual ||b - D x|| / ||b|| <= tol per RHS, through
+ * the even-odd Schur complement: bhat_e = b_e - D_eo D_oo^{-1} b_o,
+ * Mhat x_e = bhat_e, x_o = D_oo^{-1}(b_o - D_oe x_e).
+ * b, x: complex128 [nrhs][V][4][3], in device memory or in host memory (then
+ * copied in and out inside the call).  csw != 0 requires bpp_clover_build with
+ * the same kappa and csw.  stats: NULL or an array of nrhs entries.
+ * Synchronises `stream` (convergence decisions are taken on the host).
+ * Errors: INVALID_ARG, UNSUPPORTED, NOT_CONVERGED (x holds the best iterate),
+ * NONFINITE, OOM, CUDA. */
+int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs,
+              const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream);
+
+/* Batched solve over nlat independent lattices (each with its own gauge
+ * handle, hopping parameter and one right-hand side; Wilson, csw = 0), run
+ * together so every kernel launch covers all lattices.  b[i], x[i]: device
+ * complex128 [V_i][4][3].  stats: NULL or nlat entries.
+ * Errors: as bpp_solve. */
+int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* const* x,
+                    const double* kappa, double tol, const bpp_solve_opts* opts,
+                    bpp_solve_stats* stats, bpp_stream stream);
+
+/* Link gradient of L = Re<eta, D^{-1} b> for the Wilson hopping term, given
+ * x = D^{-1} b and lam = D^{-dag} eta (complex128 [V][4][3], device):
+ *   G_mu(x) = kappa * bc * M_mu(x)^dag,
+ *   M_mu(x) = sum_spin [ x(x+mu) ((1 - gamma_mu) lam(x))^dag + ((1 + gamma_mu) lam(x+mu)) x(x)^dag ]
+ * (dL = -Re<lam, dD x> with dD read off Eq. (1)).  With project_su3 != 0 the
+ * output is instead the traceless Hermitian force
+ *   P_mu(x) = (i/2)(U G^dag - G U^dag) - trace/3,  so that dL/deps = tr(T P)
+ * for U_mu(x) -> exp(i eps T) U_mu(x).
+ * dU: complex128 [4][V][3][3], device, caller-owned.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, void* dU, int project_su3,
+              bpp_stream stream);
+
+/* Number of kernels this library has launched since load (or since the last
+ * reset when reset != 0); graph launches count each kernel node they run. */
+int64_t bpp_launch_count(int reset);
+
+/* Kernel timing: while enabled, every launch of the even-odd hopping kernels
+ * outside a CUDA graph is bracketed by CUDA events on its stream. */
+int bpp_prof_enable(int enable);
+/* Reads (and with reset != 0 clears) the accumulated hopping-kernel timings for
+ * precision prec: number of launches, total milliseconds, total algorithmic
+ * bytes.  Synchronises the device. */
+int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int reset);
+
+/* Releases cached device workspace (synchronises the device). */
+int bpp_release_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPP_H_ */

@@ -1,0 +1,328 @@
+"""B300 Wilson / Wilson-clover fermion matrix and solver (arXiv:2111.04457, Eq. 1).
+
+Thin Python binding over the C ABI in include/bpp.h (libbpp.so): argument
+marshalling only.  Every step of the computation runs in the library's CUDA
+kernels; PyTorch supplies device memory and streams.  There is no CPU path:
+importing this module fails loudly when libbpp.so is missing, and every call
+needs CUDA tensors (the solve also accepts host tensors, copied inside the
+call).
+
+Canonical layouts (see include/bpp.h): spinors complex [nrhs][V][4][3] (half
+fields [nrhs][Vh][4][3], sites of one parity in lexicographic order), links
+complex128 [4][V][3][3], lexicographic site index x1 + L1*(x2 + L2*(x3 + L3*x4)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libbpp.so")
+
+if not os.path.exists(_SO):
+    raise ImportError(f"libbpp.so not found at {_SO}: build it with "
+                      "`python paper_2111_04457_b300/build.py` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(_SO)
+
+F64, F32, F16 = 0, 1, 2
+EVEN, ODD, FULL = 0, 1, 2
+BICGSTAB, CGNR = 0, 1
+_ERR = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
+        -6: "NONFINITE", -7: "TIMEOUT"}
+
+
+class BppError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class NotConverged(BppError):
+    pass
+
+
+class _Lattice(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("bc", ctypes.c_int * 4)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("use_x0", ctypes.c_int),
+                ("dagger", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("status", ctypes.c_int), ("true_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_p, _i, _d, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+_SIGS = {
+    "bpp_version": ([], _i),
+    "bpp_last_error": ([ctypes.c_char_p, ctypes.c_size_t], _i),
+    "bpp_gauge_create": ([ctypes.POINTER(_Lattice), _p, _p, ctypes.POINTER(_p)], _i),
+    "bpp_gauge_destroy": ([_p], _i),
+    "bpp_clover_build": ([_p, _d, _d, _p], _i),
+    "bpp_dslash": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
+    "bpp_clover_apply": ([_p, _p, _p, _i, _i, _i, _i, _p], _i),
+    "bpp_schur_apply": ([_p, _p, _p, _d, _d, _i, _i, _i, _p], _i),
+    "bpp_dirac_apply": ([_p, _p, _p, _d, _d, _i, _i, _p], _i),
+    "bpp_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
+    "bpp_solve": ([_p, _p, _p, _d, _d, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
+    "bpp_solve_batch": ([_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_d), _d,
+                         ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
+    "bpp_force": ([_p, _p, _p, _d, _p, _i, _p], _i),
+    "bpp_launch_count": ([_i], _i64),
+    "bpp_prof_enable": ([_i], _i),
+    "bpp_prof_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), ctypes.POINTER(_d), _i], _i),
+    "bpp_release_workspace": ([], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _check(rc):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(1024)
+        _lib.bpp_last_error(buf, 1024)
+        cls = NotConverged if rc == -5 else BppError
+        raise cls(rc, buf.value.decode(errors="replace"))
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _cuda(t: torch.Tensor, what):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (the library has no CPU path)")
+
+
+def _cdtype(prec):
+    return torch.complex128 if prec == F64 else torch.complex64
+
+
+def version() -> int:
+    return _lib.bpp_version()
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(_lib.bpp_launch_count(int(reset)))
+
+
+def prof_enable(on: bool = True):
+    _check(_lib.bpp_prof_enable(int(on)))
+
+
+def prof_read(prec: int, reset: bool = True):
+    """(launches, total_ms, total_algorithmic_bytes) of the hopping kernels of precision prec."""
+    n, ms, by = _i64(), _d(), _d()
+    _check(_lib.bpp_prof_read(prec, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), int(reset)))
+    return n.value, ms.value, by.value
+
+
+def release_workspace():
+    _check(_lib.bpp_release_workspace())
+
+
+@dataclass(frozen=True)
+class Lattice:
+    L: tuple
+    bc: tuple = (1, 1, 1, -1)
+
+    @property
+    def V(self):
+        return self.L[0] * self.L[1] * self.L[2] * self.L[3]
+
+    @property
+    def Vh(self):
+        return self.V // 2
+
+
+class Gauge:
+    """Gauge field U_mu(x) on the device in the library's internal layout.
+
+    U: complex128 tensor [4][V][3][3] (CUDA or CPU; copied)."""
+
+    def __init__(self, U: torch.Tensor, L, bc=(1, 1, 1, -1), stream=None):
+        self.lattice = Lattice(tuple(int(v) for v in L), tuple(int(v) for v in bc))
+        if U.dtype != torch.complex128 or tuple(U.shape) != (4, self.lattice.V, 3, 3):
+            raise ValueError("U must be complex128 of shape (4, V, 3, 3)")
+        U = U.contiguous()
+        lat = _Lattice((ctypes.c_int * 4)(*self.lattice.L), (ctypes.c_int * 4)(*self.lattice.bc))
+        h = _p()
+        _check(_lib.bpp_gauge_create(ctypes.byref(lat), _ptr(U), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.clover = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("gauge handle destroyed")
+        return self._h
+
+    def clover_build(self, kappa: float, csw: float, stream=None):
+        _check(_lib.bpp_clover_build(self.handle, float(kappa), float(csw), _stream(stream)))
+        self.clover = (float(kappa), float(csw))
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.bpp_gauge_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _nrhs(t, per):
+    n = t.numel() // per
+    if n * per != t.numel() or n < 1:
+        raise ValueError("field size is not a multiple of the per-RHS size")
+    return n
+
+
+def dslash(g: Gauge, psi: torch.Tensor, kappa: float, parity: int, prec: int = F64, stream=None):
+    """parity EVEN/ODD: out_p = -kappa H_{p,pbar} psi_pbar on half fields [nrhs][Vh][4][3];
+    parity FULL: out = D_W psi (clover-free) on full fields [nrhs][V][4][3]."""
+    _cuda(psi, "psi")
+    if psi.dtype != _cdtype(prec):
+        raise ValueError(f"psi must be {_cdtype(prec)} for precision {prec}")
+    per = 12 * (g.lattice.V if parity == FULL else g.lattice.Vh)
+    n = _nrhs(psi, per)
+    psi = psi.contiguous()
+    out = torch.empty_like(psi)
+    _check(_lib.bpp_dslash(g.handle, _ptr(psi), _ptr(out), float(kappa), parity, prec, n, _stream(stream)))
+    return out
+
+
+def clover_apply(g: Gauge, x: torch.Tensor, parity: int, inverse: bool = False, prec: int = F64, stream=None):
+    """(1 + F) x or (1 + F)^-1 x on half fields of parity EVEN/ODD."""
+    _cuda(x, "x")
+    if x.dtype != _cdtype(prec):
+        raise ValueError(f"x must be {_cdtype(prec)}")
+    x = x.contiguous()
+    n = _nrhs(x, 12 * g.lattice.Vh)
+    out = torch.empty_like(x)
+    _check(_lib.bpp_clover_apply(g.handle, _ptr(x), _ptr(out), parity, int(inverse), prec, n, _stream(stream)))
+    return out
+
+
+def schur_apply(g: Gauge, x: torch.Tensor, kappa: float, csw: float = 0.0, dagger: bool = False, prec: int = F64,
+                stream=None):
+    """Mhat x_e = A_ee x_e - kappa^2 H_eo A_oo^-1 H_oe x_e (or its adjoint) on even half fields."""
+    _cuda(x, "x")
+    if x.dtype != _cdtype(prec):
+        raise ValueError(f"x must be {_cdtype(prec)}")
+    x = x.contiguous()
+    n = _nrhs(x, 12 * g.lattice.Vh)
+    out = torch.empty_like(x)
+    _check(_lib.bpp_schur_apply(g.handle, _ptr(x), _ptr(out), float(kappa), float(csw), int(dagger), prec, n,
+                                _stream(stream)))
+    return out
+
+
+def dirac_apply(g: Gauge, x: torch.Tensor, kappa: float, csw: float = 0.0, dagger: bool = False, stream=None):
+    """D x (or D^dag x) of Eq. (1) in FP64 on full complex128 fields [nrhs][V][4][3]."""
+    _cuda(x, "x")
+    if x.dtype != torch.complex128:
+        raise ValueError("x must be complex128")
+    x = x.contiguous()
+    n = _nrhs(x, 12 * g.lattice.V)
+    out = torch.empty_like(x)
+    _check(_lib.bpp_dirac_apply(g.handle, _ptr(x), _ptr(out), float(kappa), float(csw), int(dagger), n,
+                                _stream(stream)))
+    return out
+
+
+def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000, max_outer=50, dagger=False,
+               check_every=16, use_x0=False) -> SolveOpts:
+    o = SolveOpts()
+    _lib.bpp_solve_opts_default(ctypes.byref(o))
+    o.solver = solver
+    o.inner_prec = inner_prec
+    if inner_tol is not None:
+        o.inner_tol = inner_tol
+    elif inner_prec == F16:
+        o.inner_tol = 5e-3
+    o.max_inner = max_inner
+    o.max_outer = max_outer
+    o.dagger = int(dagger)
+    o.check_every = check_every
+    o.use_x0 = int(use_x0)
+    return o
+
+
+def solve(g: Gauge, b: torch.Tensor, kappa: float, csw: float = 0.0, tol: float = 1e-10, opts: SolveOpts = None,
+          x: torch.Tensor = None, stream=None, raise_on_fail: bool = True):
+    """x = D^-1 b (or D^-dag b with opts.dagger) to ||b - D x|| / ||b|| <= tol per RHS.
+    b: complex128 [nrhs][V][4][3] (or [V][4][3]) on the device or the host.
+    Returns (x, [stats dict per RHS])."""
+    if b.dtype != torch.complex128:
+        raise ValueError("b must be complex128")
+    b = b.contiguous()
+    n = _nrhs(b, 12 * g.lattice.V)
+    if x is None:
+        x = torch.empty_like(b)
+    o = opts if opts is not None else solve_opts()
+    st = (SolveStats * n)()
+    rc = _lib.bpp_solve(g.handle, _ptr(b), _ptr(x), float(kappa), float(csw), float(tol), n, ctypes.byref(o), st,
+                        _stream(stream))
+    stats = [s.as_dict() for s in st]
+    if raise_on_fail:
+        _check(rc)
+    return x, stats
+
+
+def solve_batch(gauges, bs, kappas, tol: float = 1e-10, opts: SolveOpts = None, xs=None, stream=None,
+                raise_on_fail: bool = True):
+    """Independent Wilson solves on several lattices run together in every launch."""
+    n = len(gauges)
+    xs = [torch.empty_like(b) for b in bs] if xs is None else xs
+    for b in bs:
+        _cuda(b, "b")
+    H = (_p * n)(*[g.handle for g in gauges])
+    B = (_p * n)(*[_ptr(b).value for b in bs])
+    X = (_p * n)(*[_ptr(x).value for x in xs])
+    K = (_d * n)(*[float(k) for k in kappas])
+    o = opts if opts is not None else solve_opts()
+    st = (SolveStats * n)()
+    rc = _lib.bpp_solve_batch(n, H, B, X, K, float(tol), ctypes.byref(o), st, _stream(stream))
+    stats = [s.as_dict() for s in st]
+    if raise_on_fail:
+        _check(rc)
+    return xs, stats
+
+
+def force(g: Gauge, x: torch.Tensor, lam: torch.Tensor, kappa: float, project: bool = False, stream=None):
+    """Link gradient G (project=False) or projected force P (project=True) of
+    L = Re<eta, D^-1 b>, given x = D^-1 b and lam = D^-dag eta (complex128 [V][4][3])."""
+    _cuda(x, "x")
+    _cuda(lam, "lam")
+    x, lam = x.contiguous(), lam.contiguous()
+    out = torch.empty((4, g.lattice.V, 3, 3), dtype=torch.complex128, device=x.device)
+    _check(_lib.bpp_force(g.handle, _ptr(x), _ptr(lam), float(kappa), _ptr(out), int(project), _stream(stream)))
+    return out
+
+
+def exported_symbols():
+    """Names of the C functions this binding binds (all declared in include/bpp.h)."""
+    return sorted(_SIGS)

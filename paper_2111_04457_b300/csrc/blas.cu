@@ -1,0 +1,473 @@
+// Batched BLAS-1 with fused reductions for the solvers; see blas.h.
+#include <string>
+
+#include "blas.h"
+#include "kernels.h"
+
+namespace bpp {
+
+constexpr int BLAS_B = 256;
+
+__host__ __device__ __forceinline__ double2 c2(double r, double i) { return make_double2(r, i); }
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) { return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return c2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+void RedBuf::ensure(int nblocks, int nsys, cudaStream_t st) {
+    if (nblocks > cap_blocks) {
+        partials.alloc((size_t)nblocks * 4 * sizeof(double), st);
+        cap_blocks = nblocks;
+    }
+    if (tickets.n < (size_t)MAXSYS * sizeof(unsigned)) {
+        tickets.alloc((size_t)MAXSYS * sizeof(unsigned), st);
+        BPP_CUDA(cudaMemsetAsync(tickets.p, 0, (size_t)MAXSYS * sizeof(unsigned), st));
+    }
+}
+
+struct BlasParams {
+    const SysDesc* sys;
+    BlockMap map;
+    BlasVecs v;
+    KScal* sc;
+    double* partials;
+    unsigned* tickets;
+};
+
+// Block-wide sum of NR doubles, then the last block of system s sums all the
+// system's block partials in block order; returns true in every thread of
+// that last block, with tot[] valid in thread 0.
+template <int NR>
+__device__ bool reduce_sys(const BlasParams& bp, int s, double v[NR], double tot[NR]) {
+    __shared__ double sh[32][NR];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double a = v[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[warp][k] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double a = 0.0;
+            for (int w = 0; w < nw; ++w) a += sh[w][k];
+            bp.partials[(size_t)blockIdx.x * NR + k] = a;
+        }
+        __threadfence();
+        const int nb = bp.map.uniform ? bp.map.tiles_per_sys : bp.map.tile_start[s + 1] - bp.map.tile_start[s];
+        const unsigned t = atomicAdd(&bp.tickets[s], 1u);
+        last = (t == (unsigned)(nb - 1));
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    const int nb = bp.map.uniform ? bp.map.tiles_per_sys : bp.map.tile_start[s + 1] - bp.map.tile_start[s];
+    double a[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) a[k] = 0.0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        const int blk = bp.map.uniform ? s + bp.map.nsys * t : bp.map.tile_start[s] + t;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) a[k] += __ldcg(&bp.partials[(size_t)blk * NR + k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double b = a[k];
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+        if (lane == 0) sh[warp][k] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double b = 0.0;
+            for (int w = 0; w < nw; ++w) b += sh[w][k];
+            tot[k] = b;
+        }
+        bp.tickets[s] = 0u;
+    }
+    return true;
+}
+
+template <class real>
+__device__ __forceinline__ void dot12(const cx<real> a[12], const cx<real> b[12], real& re, real& im) {
+    re = 0; im = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        re = fma(a[k].r, b[k].r, re); re = fma(a[k].i, b[k].i, re);
+        im = fma(a[k].r, b[k].i, im); im = fma(-a[k].i, b[k].r, im);
+    }
+}
+template <class real>
+__device__ __forceinline__ real norm12(const cx<real> a[12]) {
+    real n = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { n = fma(a[k].r, a[k].r, n); n = fma(a[k].i, a[k].i, n); }
+    return n;
+}
+
+__device__ __forceinline__ void check_done(KScal& k) {
+    if (!isfinite(k.rr)) { k.done = 1; k.status = 3; return; }
+    if (k.rr <= k.tol2 * k.bb) { k.done = 1; return; }
+    if (k.iter >= k.max_iter) { k.done = 1; k.status = 2; }
+}
+
+template <int P, int OP>
+__global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
+    using real = typename PT<P>::real;
+    using A = Access<P>;
+    int s, tile;
+    map_block(bp.map, s, tile);
+    const SysDesc& d = bp.sys[s];
+    KScal* K = bp.sc + s;
+    const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2) || !K->done;
+    const int i = tile * blockDim.x + threadIdx.x;
+    const bool in = active && i < d.g.Vh;
+    // scalars used by the update (read before any finalize of this launch)
+    const double2 al = K->alpha, om = K->omega, be = K->beta;
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    if (in) {
+        cx<real> a[12], b[12], c[12];
+        if (OP == B_INIT_BICG) {
+            A::load_spinor(sys_view<P>(bp.v.b, d), i, a);
+            A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
+            A::store_spinor(sys_view<P>(bp.v.rhat, d), i, a);
+            A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
+            A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
+            red[0] = (double)norm12(a);
+        } else if (OP == B_ALPHA) {
+            real re, im;
+            A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.v, d), i, b);
+            dot12(a, b, re, im);
+            red[0] = re; red[1] = im;
+        } else if (OP == B_S) {
+            const cx<real> alr = mkc<real>((real)al.x, (real)al.y);
+            A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.v, d), i, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) { c[k] = a[k]; cfma(c[k], -alr, b[k]); }
+            A::store_spinor(sys_view<P>(bp.v.s, d), i, c);
+        } else if (OP == B_OMEGA) {
+            real re, im;
+            A::load_spinor(sys_view<P>(bp.v.t, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.s, d), i, b);
+            dot12(a, b, re, im);
+            red[0] = re; red[1] = im; red[2] = (double)norm12(a);
+        } else if (OP == B_XR) {
+            const cx<real> alr = mkc<real>((real)al.x, (real)al.y), omr = mkc<real>((real)om.x, (real)om.y);
+            // x += alpha p + omega s
+            A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+            A::load_spinor(sys_view<P>(bp.v.s, d), i, c);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) { cfma(a[k], alr, b[k]); cfma(a[k], omr, c[k]); }
+            A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
+            // r = s - omega t
+            A::load_spinor(sys_view<P>(bp.v.t, d), i, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) cfma(c[k], -omr, b[k]);
+            A::store_spinor(sys_view<P>(bp.v.r, d), i, c);
+            A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
+            real re, im;
+            dot12(a, c, re, im);
+            red[0] = norm12(c); red[1] = re; red[2] = im;
+        } else if (OP == B_P) {
+            const cx<real> ber = mkc<real>((real)be.x, (real)be.y), omr = mkc<real>((real)om.x, (real)om.y);
+            A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+            A::load_spinor(sys_view<P>(bp.v.v, d), i, c);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cfma(b[k], -omr, c[k]);     // p - omega v
+                cfma(a[k], ber, b[k]);      // r + beta (...)
+            }
+            A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+        } else if (OP == B_CG_INIT) {
+            A::load_spinor(sys_view<P>(bp.v.b, d), i, a);
+            A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
+            A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
+            red[0] = (double)norm12(a);
+        } else if (OP == B_CG_PZ) {
+            A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
+            A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+            red[0] = (double)norm12(a);
+        } else if (OP == B_CG_ALPHA) {
+            A::load_spinor(sys_view<P>(bp.v.w, d), i, a);
+            red[0] = (double)norm12(a);
+        } else if (OP == B_CG_XR) {
+            const real alr = (real)al.x;
+            A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a[k] = a[k] + alr * b[k];
+            A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
+            A::load_spinor(sys_view<P>(bp.v.w, d), i, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a[k] = a[k] - alr * b[k];
+            A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
+            red[0] = (double)norm12(a);
+        } else if (OP == B_CG_BETA) {
+            A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
+            red[0] = (double)norm12(a);
+        } else if (OP == B_NORM2) {
+            A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+            red[0] = (double)norm12(a);
+        }
+    }
+    constexpr bool HAS_RED = OP != B_S && OP != B_P;
+    if (!HAS_RED) return;
+    if (!active) return;   // whole system inactive: every block of it returns here
+    double tot[4];
+    if (!reduce_sys<4>(bp, s, red, tot)) return;
+    if (threadIdx.x != 0) return;
+    KScal& k = *K;
+    if (OP == B_INIT_BICG) {
+        k.bb = tot[0];
+        k.rr = tot[0];
+        k.rho = c2(tot[0], 0.0);
+        k.alpha = c2(1.0, 0.0);
+        k.omega = c2(1.0, 0.0);
+        k.beta = c2(0.0, 0.0);
+        k.iter = 0;
+        k.status = 0;
+        k.done = 0;
+        check_done(k);
+        if (k.bb == 0.0) { k.done = 1; k.status = 0; }
+    } else if (OP == B_ALPHA) {
+        k.rv = c2(tot[0], tot[1]);
+        if (cabs2(k.rv) == 0.0 || !isfinite(k.rv.x)) { k.status = 1; k.done = 1; k.alpha = c2(0, 0); }
+        else k.alpha = cdiv2(k.rho, k.rv);
+    } else if (OP == B_OMEGA) {
+        k.ts = c2(tot[0], tot[1]);
+        k.tt = tot[2];
+        k.omega = k.tt > 0.0 ? c2(k.ts.x / k.tt, k.ts.y / k.tt) : c2(0.0, 0.0);
+    } else if (OP == B_XR) {
+        k.rr = tot[0];
+        const double2 rho_new = c2(tot[1], tot[2]);
+        k.iter += 1;
+        if (cabs2(k.omega) == 0.0) { k.status = 1; k.done = 1; }
+        else k.beta = cmul2(cdiv2(rho_new, k.rho), cdiv2(k.alpha, k.omega));
+        k.rho = rho_new;
+        if (cabs2(rho_new) < 1e-60 * k.rr * k.bb && !(k.rr <= k.tol2 * k.bb)) { k.status = 1; k.done = 1; }
+        check_done(k);
+    } else if (OP == B_CG_INIT) {
+        k.bb = tot[0];
+        k.rr = tot[0];
+        k.iter = 0;
+        k.status = 0;
+        k.done = 0;
+        check_done(k);
+        if (k.bb == 0.0) { k.done = 1; k.status = 0; }
+    } else if (OP == B_CG_PZ) {
+        k.zz = tot[0];
+    } else if (OP == B_CG_ALPHA) {
+        if (tot[0] > 0.0) k.alpha = c2(k.zz / tot[0], 0.0);
+        else { k.alpha = c2(0.0, 0.0); k.status = 1; k.done = 1; }
+    } else if (OP == B_CG_XR) {
+        k.rr = tot[0];
+        k.iter += 1;
+        check_done(k);
+    } else if (OP == B_CG_BETA) {
+        k.beta = c2(k.zz > 0.0 ? tot[0] / k.zz : 0.0, 0.0);
+        k.zz = tot[0];
+    } else if (OP == B_NORM2) {
+        k.bb = tot[0];
+    }
+}
+
+// p = z + beta p for CGNR (separate: needs the finalised beta)
+template <int P>
+__global__ void __launch_bounds__(BLAS_B) k_cg_p(BlasParams bp) {
+    using real = typename PT<P>::real;
+    int s, tile;
+    map_block(bp.map, s, tile);
+    const SysDesc& d = bp.sys[s];
+    if (bp.sc[s].done) return;
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    const real be = (real)bp.sc[s].beta.x;
+    cx<real> a[12], b[12];
+    Access<P>::load_spinor(sys_view<P>(bp.v.z, d), i, a);
+    Access<P>::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a[k] = a[k] + be * b[k];
+    Access<P>::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+}
+
+template <int P>
+static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st) {
+    BlasParams bp;
+    bp.sys = bt.dev();
+    int nb = 0;
+    bp.map = block_map(bt, BLAS_B, nb);
+    rb.ensure(nb, bt.nsys(), st);
+    bp.v = vv;
+    bp.sc = sc;
+    bp.partials = rb.partials.as<double>();
+    bp.tickets = rb.tickets.as<unsigned>();
+    switch (op) {
+        case B_INIT_BICG: k_blas<P, B_INIT_BICG><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_ALPHA: k_blas<P, B_ALPHA><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_S: k_blas<P, B_S><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_OMEGA: k_blas<P, B_OMEGA><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_XR: k_blas<P, B_XR><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_P: k_blas<P, B_P><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_CG_INIT: k_blas<P, B_CG_INIT><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_CG_PZ: k_blas<P, B_CG_PZ><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_CG_ALPHA: k_blas<P, B_CG_ALPHA><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_CG_XR: k_blas<P, B_CG_XR><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_CG_BETA:
+            k_blas<P, B_CG_BETA><<<nb, BLAS_B, 0, st>>>(bp);
+            count_launch();
+            k_cg_p<P><<<nb, BLAS_B, 0, st>>>(bp);
+            break;
+        case B_NORM2: k_blas<P, B_NORM2><<<nb, BLAS_B, 0, st>>>(bp); break;
+        default: throw Error(BPP_ERR_INVALID_ARG, "bad blas op");
+    }
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st) {
+    if (bt.prec == P64) blas_t<P64>(bt, op, vv, sc, rb, st);
+    else if (bt.prec == P32) blas_t<P32>(bt, op, vv, sc, rb, st);
+    else blas_t<P16>(bt, op, vv, sc, rb, st);
+}
+
+// ----------------------------------------------------------------------------- outer loop
+struct OuterParams {
+    const SysDesc* s64;
+    const SysDesc* sP;
+    BlockMap map;
+    char* a;
+    char* b;
+    KScal* sc;
+    double* partials;
+    unsigned* tickets;
+};
+
+__global__ void __launch_bounds__(BLAS_B) k_outer_residual(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    double red[4] = {0, 0, 0, 0};
+    if (i < d.g.Vh) {
+        cx<double> bh[12], r[12];
+        Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, bh);
+        Access<P64>::load_spinor(sys_view<P64>(op.b, d), i, r);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r[k] = bh[k] - r[k];
+        Access<P64>::store_spinor(sys_view<P64>(op.b, d), i, r);
+        red[0] = norm12(r);
+    }
+    BlasParams bp;
+    bp.map = op.map;
+    bp.partials = op.partials;
+    bp.tickets = op.tickets;
+    double tot[4];
+    if (!reduce_sys<4>(bp, s, red, tot)) return;
+    if (threadIdx.x == 0) {
+        op.sc[s].rr = tot[0];
+        op.sc[s].scale = sqrt(tot[0]);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(BLAS_B) k_outer_down(OuterParams op) {
+    using real = typename PT<P>::real;
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    const double sc = op.sc[s].scale;
+    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    cx<double> r[12];
+    cx<real> lo[12];
+    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, r);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) lo[k] = mkc<real>((real)(r[k].r * inv), (real)(r[k].i * inv));
+    Access<P>::store_spinor(sys_view<P>(op.b, op.sP[s]), i, lo);
+}
+
+template <int P>
+__global__ void __launch_bounds__(BLAS_B) k_outer_acc(OuterParams op) {
+    using real = typename PT<P>::real;
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    const double sc = op.sc[s].scale;
+    cx<double> x[12];
+    cx<real> e[12];
+    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, x);
+    Access<P>::load_spinor(sys_view<P>(op.b, op.sP[s]), i, e);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[k] = x[k] + sc * mkc<double>((double)e[k].r, (double)e[k].i);
+    Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, x);
+}
+
+void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = b64.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    rb.ensure(nb, b64.nsys(), st);
+    op.a = bhat;
+    op.b = r64;
+    op.sc = sc;
+    op.partials = rb.partials.as<double>();
+    op.tickets = rb.tickets.as<unsigned>();
+    k_outer_residual<<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = bP.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    op.a = const_cast<char*>(r64);
+    op.b = lo;
+    op.sc = const_cast<KScal*>(sc);
+    if (bP.prec == P64) k_outer_down<P64><<<nb, BLAS_B, 0, st>>>(op);
+    else if (bP.prec == P32) k_outer_down<P32><<<nb, BLAS_B, 0, st>>>(op);
+    else k_outer_down<P16><<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* e, const KScal* sc, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = bP.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    op.a = x64;
+    op.b = const_cast<char*>(e);
+    op.sc = const_cast<KScal*>(sc);
+    if (bP.prec == P64) k_outer_acc<P64><<<nb, BLAS_B, 0, st>>>(op);
+    else if (bP.prec == P32) k_outer_acc<P32><<<nb, BLAS_B, 0, st>>>(op);
+    else k_outer_acc<P16><<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+}  // namespace bpp

@@ -1,0 +1,72 @@
+// Fused vector updates with reductions for the Krylov solvers (BiCGStab of
+// van der Vorst 1992 and CGNR), batched over systems, with all scalars kept on
+// the device: every reduction ends in the last block of its system, which
+// sums the per-block partials in a fixed order (deterministic) and derives the
+// next solver scalars, so the host never waits inside an iteration.
+#pragma once
+
+#include "bpp_internal.h"
+#include "gauge.h"
+
+namespace bpp {
+
+// Per-system solver scalars (complex numbers as double2).
+struct KScal {
+    double2 rho;      // <rhat, r>
+    double2 alpha, omega, beta;
+    double2 rv;       // <rhat, v>
+    double2 ts;       // <t, s>
+    double tt;        // <t, t>
+    double rr;        // ||r||^2 (recursive)
+    double bb;        // ||b||^2 of the system being solved
+    double tol2;      // stop when rr <= tol2 * bb
+    double zz;        // CGNR: ||z||^2
+    double scale;     // outer loop: ||r|| of the current defect
+    int iter;
+    int max_iter;
+    int done;         // 1: converged or stopped
+    int status;       // 0 ok, 1 breakdown, 2 iteration cap, 3 non-finite
+};
+
+// Workspace for the reductions of one batch.
+struct RedBuf {
+    DevBuf partials;   // nblocks * 4 doubles
+    DevBuf tickets;    // nsys unsigned
+    int cap_blocks = 0;
+    void ensure(int nblocks, int nsys, cudaStream_t st);
+};
+
+enum BlasOp {
+    B_INIT_BICG = 0,   // r = b, rhat = b, p = b, x = 0; rho = bb = ||b||^2
+    B_ALPHA,           // alpha = rho / <rhat, v>
+    B_S,               // s = r - alpha v
+    B_OMEGA,           // omega = <t,s>/<t,t>
+    B_XR,              // x += alpha p + omega s; r = s - omega t; rho, beta, rr, done
+    B_P,               // p = r + beta (p - omega v)
+    B_CG_INIT,         // r = b, x = 0; bb = ||b||^2 (CGNR; z = Mdag r follows)
+    B_CG_PZ,           // p = z; zz = ||z||^2
+    B_CG_ALPHA,        // alpha = zz / ||w||^2
+    B_CG_XR,           // x += alpha p; r -= alpha w; rr, done
+    B_CG_BETA,         // beta = ||z||^2 / zz; zz = ||z||^2; p = z + beta p
+    B_NORM2            // bb = ||x||^2 (no update)
+};
+
+struct BlasVecs {
+    char *x = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
+         *b = nullptr, *w = nullptr, *z = nullptr;
+};
+
+void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st);
+
+// Outer defect-correction steps (FP64 batch b64 and inner-precision batch bP
+// over the same systems):
+// r64 = bhat - r64 (r64 holds Mhat x on entry); sc.rr = ||r64||^2, sc.scale = ||r64||
+void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st);
+// lo = r64 / scale (converted to the inner precision)
+void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st);
+// x64 += scale * e (e in the inner precision)
+void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* e, const KScal* sc, cudaStream_t st);
+// out = a * in + y (same precision), a per system given on the host
+void axpy_copy(const Batch& b, const char* in, char* out, cudaStream_t st);
+
+}  // namespace bpp

@@ -1,0 +1,259 @@
+// Even-odd hopping term of Eq. (1) (Sec. 3): for every site x of parity p,
+//
+//   hop(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu^dag(x-mu) psi(x-mu) ]
+//
+// (projectors swapped for the adjoint), with psi living on parity 1-p, and a
+// fused epilogue that forms one of
+//   PLAIN     out = a hop                      (a = +-kappa of the system)
+//   XPAY      out = y + a hop
+//   CLOV_XPAY out = A y + a hop                (A = 1 + F on parity p)
+//   INV       out = A^-1 (a hop)
+//   INV_XPAY  out = A^-1 (y + a hop)
+//
+// Each direction uses the chiral-basis structure gamma_mu = [[0, A_mu], [A_mu^dag, 0]]
+// with A_k = i sigma_k, A_4 = 1: (1 + s gamma_mu) psi = (h, s A_mu^dag h) where
+// h = u + s A_mu l (u, l the upper and lower spin pairs), so only the two-spin
+// half spinor h is multiplied by the link and the lower half is rebuilt from
+// U h with a few sign and i factors.  One thread per output site; neighbour
+// spinors come through L1/L2 (each is read by 8 sites), links stream once.
+#include <string>
+
+#include "bpp_internal.h"
+#include "clover_dev.h"
+#include "gauge.h"
+#include "kernels.h"
+
+namespace bpp {
+
+// h = u + S A_mu l for the four-spinor psi (u = spins 0,1; l = spins 2,3).
+template <int MU, int S, class real>
+__device__ __forceinline__ void project(const cx<real> psi[12], cx<real> h[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<real> u0 = psi[c], u1 = psi[3 + c], l0 = psi[6 + c], l1 = psi[9 + c];
+        if (MU == 0) {          // A l = (i l1, i l0)
+            h[c] = S > 0 ? u0 + ix(l1) : u0 - ix(l1);
+            h[3 + c] = S > 0 ? u1 + ix(l0) : u1 - ix(l0);
+        } else if (MU == 1) {   // A l = (l1, -l0)
+            h[c] = S > 0 ? u0 + l1 : u0 - l1;
+            h[3 + c] = S > 0 ? u1 - l0 : u1 + l0;
+        } else if (MU == 2) {   // A l = (i l0, -i l1)
+            h[c] = S > 0 ? u0 + ix(l0) : u0 - ix(l0);
+            h[3 + c] = S > 0 ? u1 - ix(l1) : u1 + ix(l1);
+        } else {                // A l = (l0, l1)
+            h[c] = S > 0 ? u0 + l0 : u0 - l0;
+            h[3 + c] = S > 0 ? u1 + l1 : u1 - l1;
+        }
+    }
+}
+
+// acc += (g, S A_mu^dag g) for the colour-multiplied half spinor g.
+template <int MU, int S, class real>
+__device__ __forceinline__ void reconstruct(cx<real> acc[12], const cx<real> g[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<real> g0 = g[c], g1 = g[3 + c];
+        acc[c] = acc[c] + g0;
+        acc[3 + c] = acc[3 + c] + g1;
+        if (MU == 0) {          // A^dag g = (-i g1, -i g0)
+            acc[6 + c] = S > 0 ? acc[6 + c] - ix(g1) : acc[6 + c] + ix(g1);
+            acc[9 + c] = S > 0 ? acc[9 + c] - ix(g0) : acc[9 + c] + ix(g0);
+        } else if (MU == 1) {   // A^dag g = (-g1, g0)
+            acc[6 + c] = S > 0 ? acc[6 + c] - g1 : acc[6 + c] + g1;
+            acc[9 + c] = S > 0 ? acc[9 + c] + g0 : acc[9 + c] - g0;
+        } else if (MU == 2) {   // A^dag g = (-i g0, i g1)
+            acc[6 + c] = S > 0 ? acc[6 + c] - ix(g0) : acc[6 + c] + ix(g0);
+            acc[9 + c] = S > 0 ? acc[9 + c] + ix(g1) : acc[9 + c] - ix(g1);
+        } else {                // A^dag g = (g0, g1)
+            acc[6 + c] = S > 0 ? acc[6 + c] + g0 : acc[6 + c] - g0;
+            acc[9 + c] = S > 0 ? acc[9 + c] + g1 : acc[9 + c] - g1;
+        }
+    }
+}
+
+// g = U h (BACK = false) or U^dag h (BACK = true) on both spins of h.
+template <bool BACK, class real>
+__device__ __forceinline__ void link_mul(const cx<real> U[9], const cx<real> h[6], cx<real> g[6]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<real> t = mkc<real>(0, 0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (BACK) cfmac(t, U[3 * b + a], h[3 * s + b]);
+                else cfma(t, U[3 * a + b], h[3 * s + b]);
+            }
+            g[3 * s + a] = t;
+        }
+}
+
+template <int P, int MU, int S, bool BACK>
+__device__ __forceinline__ void hop_dir(cx<typename PT<P>::real> acc[12], const SpinorView& in, int64_t j,
+                                        const LinkView& U, int64_t ju, bool flip) {
+    using real = typename PT<P>::real;
+    cx<real> psi[12], h[6], g[6], u[9];
+    Access<P>::load_spinor(in, j, psi);
+    Access<P>::load_link(U, ju, u);
+    project<MU, S>(psi, h);
+    if (flip) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = -h[k];
+    }
+    link_mul<BACK>(u, h, g);
+    reconstruct<MU, S>(acc, g);
+}
+
+// FP64 needs more registers per thread than a 512-thread block allows.
+template <int P> struct HopMaxThreads { static constexpr int value = 512; };
+template <> struct HopMaxThreads<P64> { static constexpr int value = 256; };
+
+template <int P, bool DAG, int MODE>
+__global__ void __launch_bounds__(HopMaxThreads<P>::value) k_hop(HopParams hp) {
+    using real = typename PT<P>::real;
+    int s, tile;
+    map_block(hp.map, s, tile);
+    const SysDesc& d = hp.sys[s];
+    const Geom g = d.g;
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    const int p = hp.parity, q = 1 - p;
+
+    const int x1h = i % g.Lh;
+    const int r = i / g.Lh;
+    const int x2 = r % g.L[1];
+    const int r2 = r / g.L[1];
+    const int x3 = r2 % g.L[2];
+    const int x4 = r2 / g.L[2];
+    const int x1 = 2 * x1h + ((p + x2 + x3 + x4) & 1);
+
+    const SpinorView in = sys_view<P>(hp.in, d);
+    cx<real> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = mkc<real>(0, 0);
+
+    constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
+    constexpr int SB = -SF;             // backward projector
+    // mu = 0 (x1): neighbours stay in the same row r
+    {
+        const bool wf = x1 == g.L[0] - 1, wb = x1 == 0;
+        const int jf = ((wf ? 0 : x1 + 1) >> 1) + g.Lh * r;
+        const int jb = ((wb ? g.L[0] - 1 : x1 - 1) >> 1) + g.Lh * r;
+        hop_dir<P, 0, SF, false>(acc, in, jf, d.U[p][0], i, wf && g.bc[0] < 0);
+        hop_dir<P, 0, SB, true>(acc, in, jb, d.U[q][0], jb, wb && g.bc[0] < 0);
+    }
+    {   // mu = 1 (x2)
+        const bool wf = x2 == g.L[1] - 1, wb = x2 == 0;
+        const int jf = x1h + g.Lh * (wf ? r - (g.L[1] - 1) : r + 1);
+        const int jb = x1h + g.Lh * (wb ? r + (g.L[1] - 1) : r - 1);
+        hop_dir<P, 1, SF, false>(acc, in, jf, d.U[p][1], i, wf && g.bc[1] < 0);
+        hop_dir<P, 1, SB, true>(acc, in, jb, d.U[q][1], jb, wb && g.bc[1] < 0);
+    }
+    {   // mu = 2 (x3)
+        const int st = g.L[1];
+        const bool wf = x3 == g.L[2] - 1, wb = x3 == 0;
+        const int jf = x1h + g.Lh * (wf ? r - (g.L[2] - 1) * st : r + st);
+        const int jb = x1h + g.Lh * (wb ? r + (g.L[2] - 1) * st : r - st);
+        hop_dir<P, 2, SF, false>(acc, in, jf, d.U[p][2], i, wf && g.bc[2] < 0);
+        hop_dir<P, 2, SB, true>(acc, in, jb, d.U[q][2], jb, wb && g.bc[2] < 0);
+    }
+    {   // mu = 3 (x4)
+        const int st = g.L[1] * g.L[2];
+        const bool wf = x4 == g.L[3] - 1, wb = x4 == 0;
+        const int jf = x1h + g.Lh * (wf ? r - (g.L[3] - 1) * st : r + st);
+        const int jb = x1h + g.Lh * (wb ? r + (g.L[3] - 1) * st : r - st);
+        hop_dir<P, 3, SF, false>(acc, in, jf, d.U[p][3], i, wf && g.bc[3] < 0);
+        hop_dir<P, 3, SB, true>(acc, in, jb, d.U[q][3], jb, wb && g.bc[3] < 0);
+    }
+
+    const real a = (real)(hp.a_sign * d.kappa);
+    cx<real> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = a * acc[k];
+    if (MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY || MODE == HOP_INV_XPAY) {
+        cx<real> y[12];
+        Access<P>::load_spinor(sys_view<P>(hp.y, d), i, y);
+        if (MODE == HOP_CLOV_XPAY) {
+            cx<real> ay[12];
+            clover_apply_site<P>(d.A[p], i, y, ay);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = v[k] + ay[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = v[k] + y[k];
+        }
+    }
+    if (MODE == HOP_INV || MODE == HOP_INV_XPAY) {
+        cx<real> w[12];
+        clover_apply_site<P>(d.Ainv[p], i, v, w);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = w[k];
+    }
+    Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
+}
+
+double hop_bytes_per_site(int prec, int mode) {
+    const double S = spinor_bytes(prec), L = link_bytes(prec);
+    const double C = prec == P64 ? 576 : prec == P32 ? 288 : 144;
+    double b = 8 * L + 2 * S;
+    if (mode == HOP_XPAY) b += S;
+    if (mode == HOP_CLOV_XPAY) b += S + C;
+    if (mode == HOP_INV) b += C;
+    if (mode == HOP_INV_XPAY) b += S + C;
+    return b;
+}
+
+template <int P, bool DAG, int MODE>
+static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* out, char* y, cudaStream_t st) {
+    HopParams hp;
+    hp.sys = b.dev();
+    hp.parity = parity;
+    hp.in = in;
+    hp.out = out;
+    hp.y = y;
+    hp.a_sign = a_sign;
+    const std::string key = "hop" + std::to_string(P) + (DAG ? "d" : "n") + std::to_string(MODE) + "_" +
+                            std::to_string(b.Vh_max) + "x" + std::to_string(b.nsys()) + (b.uniform ? "u" : "r");
+    auto run = [&](int B) {
+        int nb = 0;
+        hp.map = block_map(b, B, nb);
+        k_hop<P, DAG, MODE><<<nb, B, 0, st>>>(hp);
+    };
+    const int B = tuned_block(key, st, run, out != y && out != in, HopMaxThreads<P>::value);
+    double sites = 0;
+    for (auto& sd : b.sys) sites += sd.g.Vh;
+    ProfScope prof(P, sites * hop_bytes_per_site(P, MODE), st);
+    run(B);
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+template <int P, bool DAG>
+static void launch_mode(const Batch& b, int parity, int mode, double a_sign, char* in, char* out, char* y,
+                        cudaStream_t st) {
+    switch (mode) {
+        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st); break;
+        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st); break;
+        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st); break;
+        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st); break;
+        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st); break;
+        default: throw Error(BPP_ERR_INVALID_ARG, "bad hopping mode");
+    }
+}
+
+void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
+         cudaStream_t st) {
+    BPP_REQUIRE(in != out, BPP_ERR_INVALID_ARG, "hopping term: output aliases input");
+    if (b.prec == P64) {
+        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st)
+            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st);
+    } else if (b.prec == P32) {
+        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st)
+            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st);
+    } else {
+        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st)
+            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st);
+    }
+}
+
+}  // namespace bpp

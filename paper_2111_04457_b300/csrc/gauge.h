@@ -1,0 +1,64 @@
+// Gauge handle and host-side batch builders shared by the launchers.
+#pragma once
+
+#include <vector>
+
+#include "bpp_internal.h"
+
+struct bpp_gauge_s {
+    bpp::Geom g;
+    int64_t V = 0, Vh = 0, stride = 0;
+    int device = 0;
+    void* links[3] = {nullptr, nullptr, nullptr};   // per precision: 8 link fields [parity][mu]
+    bool has_clover = false;
+    double clov_kappa = 0.0, clov_csw = 0.0;
+    void* clover[3] = {nullptr, nullptr, nullptr};  // per precision: A_e, A_o, Ainv_e, Ainv_o
+};
+
+namespace bpp {
+
+using Gauge = bpp_gauge_s;
+
+inline size_t clover_alloc_bytes(int prec, int64_t stride) {
+    return (size_t)stride * (prec == P64 ? 576 : prec == P32 ? 288 : 144);
+}
+
+inline LinkView link_view(const Gauge& G, int prec, int parity, int mu) {
+    LinkView v;
+    v.data = static_cast<const char*>(G.links[prec]) + (size_t)(parity * 4 + mu) * link_alloc_bytes(prec, G.stride);
+    v.stride = G.stride;
+    return v;
+}
+
+// which: 0 = A, 1 = A^-1
+inline CloverView clover_view(const Gauge& G, int prec, int which, int parity) {
+    CloverView v;
+    v.stride = G.stride;
+    v.data = G.has_clover ? static_cast<const char*>(G.clover[prec]) +
+                                (size_t)(which * 2 + parity) * clover_alloc_bytes(prec, G.stride)
+                          : nullptr;
+    return v;
+}
+
+// Host description of a batch: one SysDesc per system plus the device copy.
+struct Batch {
+    int prec = P64;
+    std::vector<SysDesc> sys;
+    DevBuf dsys;
+    size_t vec_bytes = 0;   // bytes of one batch vector (all systems, one parity)
+    bool uniform = true;
+    int Vh_max = 0;
+    void upload(cudaStream_t s) {
+        dsys.alloc(sys.size() * sizeof(SysDesc), s);
+        BPP_CUDA(cudaMemcpyAsync(dsys.p, sys.data(), sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+    }
+    const SysDesc* dev() const { return dsys.as<SysDesc>(); }
+    int nsys() const { return (int)sys.size(); }
+};
+
+// Appends one system on gauge G (kappa, clover if csw != 0) to batch b.
+void batch_add(Batch& b, const Gauge& G, double kappa, bool clover);
+// Grid and block map for a launch over all systems with `sites_per_block`.
+BlockMap block_map(const Batch& b, int sites_per_block, int& nblocks);
+
+}  // namespace bpp

@@ -1,0 +1,153 @@
+// Boundary layout conversion (the "interface object" of Sec. 3.3 that
+// rearranges fields into a coalesced layout): canonical lexicographic complex
+// arrays [nsys][V or Vh][4][3] (complex128 or complex64) <-> the internal
+// per-parity structure-of-arrays half fields, with an optional gamma_5
+// (= diag(-1,-1,1,1) in the chiral basis) applied on the way.
+#include "bpp_internal.h"
+#include "gauge.h"
+#include "kernels.h"
+
+namespace bpp {
+
+template <class real> struct CanonT;
+template <> struct CanonT<double> { using type = double2; };
+template <> struct CanonT<float> { using type = float2; };
+
+template <class TC, class real>
+__device__ __forceinline__ cx<real> from_canon(TC v) { return mkc<real>((real)v.x, (real)v.y); }
+template <class TC, class real>
+__device__ __forceinline__ TC to_canon(cx<real> v);
+template <> __device__ __forceinline__ double2 to_canon<double2, double>(cx<double> v) { return make_double2(v.r, v.i); }
+template <> __device__ __forceinline__ double2 to_canon<double2, float>(cx<float> v) { return make_double2(v.r, v.i); }
+template <> __device__ __forceinline__ float2 to_canon<float2, double>(cx<double> v) { return make_float2((float)v.r, (float)v.i); }
+template <> __device__ __forceinline__ float2 to_canon<float2, float>(cx<float> v) { return make_float2(v.r, v.i); }
+
+// Thread per (half-lattice site, parity) of system sys0 + blockIdx.y.
+template <int P, class TC>
+__global__ void k_full_to_eo(const SysDesc* sys, int sys0, const TC* __restrict__ canon, int64_t cstride,
+                             char* even, char* odd, int g5) {
+    using real = typename PT<P>::real;
+    const SysDesc& d = sys[sys0 + blockIdx.y];
+    const Geom g = d.g;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * (int64_t)g.Vh) return;
+    const int p = (int)(t / g.Vh);
+    const int i = (int)(t % g.Vh);
+    int x[4];
+    eo_coords(g, i, p, x);
+    const int64_t lex = 2 * (int64_t)i + (x[0] & 1);
+    const TC* src = canon + blockIdx.y * cstride + lex * 12;
+    cx<real> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        v[k] = from_canon<TC, real>(src[k]);
+        if (g5 && k < 6) v[k] = -v[k];
+    }
+    Access<P>::store_spinor(sys_view<P>(p == 0 ? even : odd, d), i, v);
+}
+
+template <int P, class TC>
+__global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, const char* odd, TC* canon,
+                             int64_t cstride, int g5) {
+    using real = typename PT<P>::real;
+    const SysDesc& d = sys[sys0 + blockIdx.y];
+    const Geom g = d.g;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * (int64_t)g.Vh) return;
+    const int p = (int)(t / g.Vh);
+    const int i = (int)(t % g.Vh);
+    int x[4];
+    eo_coords(g, i, p, x);
+    const int64_t lex = 2 * (int64_t)i + (x[0] & 1);
+    cx<real> v[12];
+    Access<P>::load_spinor(sys_view<P>(const_cast<char*>(p == 0 ? even : odd), d), i, v);
+    TC* dst = canon + blockIdx.y * cstride + lex * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>((g5 && k < 6) ? -v[k] : v[k]);
+}
+
+// Half fields: canonical [nsys][Vh][4][3] with system s at offset s*Vh*12.
+template <int P, class TC>
+__global__ void k_half_to_int(const SysDesc* sys, const TC* __restrict__ canon, char* out) {
+    using real = typename PT<P>::real;
+    const SysDesc& d = sys[blockIdx.y];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    const TC* src = canon + ((int64_t)blockIdx.y * d.g.Vh + i) * 12;
+    cx<real> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = from_canon<TC, real>(src[k]);
+    Access<P>::store_spinor(sys_view<P>(out, d), i, v);
+}
+
+template <int P, class TC>
+__global__ void k_int_to_half(const SysDesc* sys, const char* in, TC* canon) {
+    using real = typename PT<P>::real;
+    const SysDesc& d = sys[blockIdx.y];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    cx<real> v[12];
+    Access<P>::load_spinor(sys_view<P>(const_cast<char*>(in), d), i, v);
+    TC* dst = canon + ((int64_t)blockIdx.y * d.g.Vh + i) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>(v[k]);
+}
+
+#define BPP_PREC_DISPATCH(prec, ...)                                  \
+    do {                                                              \
+        if ((prec) == P64) { constexpr int PP = P64; __VA_ARGS__; }        \
+        else if ((prec) == P32) { constexpr int PP = P32; __VA_ARGS__; }   \
+        else { constexpr int PP = P16; __VA_ARGS__; }                      \
+    } while (0)
+
+void full_to_eo(const Batch& b, int sys0, int nsys, const void* canon, int canon_f64, int64_t cstride,
+                char* even, char* odd, int g5, cudaStream_t st) {
+    const int B = 256;
+    dim3 grid((unsigned)((2 * (int64_t)b.Vh_max + B - 1) / B), nsys);
+    BPP_PREC_DISPATCH(b.prec, {
+        if (canon_f64)
+            k_full_to_eo<PP, double2><<<grid, B, 0, st>>>(b.dev(), sys0, static_cast<const double2*>(canon), cstride, even, odd, g5);
+        else
+            k_full_to_eo<PP, float2><<<grid, B, 0, st>>>(b.dev(), sys0, static_cast<const float2*>(canon), cstride, even, odd, g5);
+    });
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char* odd, void* canon, int canon_f64,
+                int64_t cstride, int g5, cudaStream_t st) {
+    const int B = 256;
+    dim3 grid((unsigned)((2 * (int64_t)b.Vh_max + B - 1) / B), nsys);
+    BPP_PREC_DISPATCH(b.prec, {
+        if (canon_f64)
+            k_eo_to_full<PP, double2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<double2*>(canon), cstride, g5);
+        else
+            k_eo_to_full<PP, float2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<float2*>(canon), cstride, g5);
+    });
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void half_to_int(const Batch& b, const void* canon, int canon_f64, char* out, cudaStream_t st) {
+    const int B = 256;
+    dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
+    BPP_PREC_DISPATCH(b.prec, {
+        if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(b.dev(), static_cast<const double2*>(canon), out);
+        else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(b.dev(), static_cast<const float2*>(canon), out);
+    });
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void int_to_half(const Batch& b, const char* in, void* canon, int canon_f64, cudaStream_t st) {
+    const int B = 256;
+    dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
+    BPP_PREC_DISPATCH(b.prec, {
+        if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<double2*>(canon));
+        else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<float2*>(canon));
+    });
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+}  // namespace bpp
