@@ -151,7 +151,10 @@ typedef struct {
     int max_outer;    /* cap on defect-correction steps */
     int use_x0;       /* nonzero: x holds the initial guess on entry */
     int dagger;       /* nonzero: solve D^dag x = b (through gamma5-hermiticity) */
-    int check_every;  /* inner iterations between host-side convergence checks */
+    int check_every;  /* inner iterations between host-side convergence checks (eager mode) */
+    int use_graph;    /* nonzero: run each inner solve as one CUDA graph launch whose
+                         conditional while node repeats one Krylov iteration until every
+                         system has converged (no host round trip per iteration) */
 } bpp_solve_opts;
 
 /* Per right-hand side statistics of a solve. */
@@ -165,7 +168,7 @@ typedef struct {
 } bpp_solve_stats;
 
 /* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 1e-5,
- * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 16. */
+ * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 1. */
 void bpp_solve_opts_default(bpp_solve_opts* opts);
 
 /* Solves D x = b (or D^dag x = b) for nrhs right-hand sides sharing the gauge

@@ -52,7 +52,7 @@ class _Lattice(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("use_x0", ctypes.c_int),
-                ("dagger", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("dagger", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -254,7 +254,7 @@ def dirac_apply(g: Gauge, x: torch.Tensor, kappa: float, csw: float = 0.0, dagge
 
 
 def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000, max_outer=50, dagger=False,
-               check_every=16, use_x0=False) -> SolveOpts:
+               check_every=4, use_x0=False, use_graph=True) -> SolveOpts:
     o = SolveOpts()
     _lib.bpp_solve_opts_default(ctypes.byref(o))
     o.solver = solver
@@ -268,6 +268,7 @@ def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000,
     o.dagger = int(dagger)
     o.check_every = check_every
     o.use_x0 = int(use_x0)
+    o.use_graph = int(use_graph)
     return o
 
 

@@ -123,6 +123,7 @@ int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream strea
 int bpp_gauge_destroy(bpp_gauge g) {
     return guard("bpp_gauge_destroy", [&]() -> int {
         if (!g) return BPP_OK;
+        drop_plans(g);
         cudaDeviceSynchronize();
         for (int p = 0; p < 3; ++p) {
             if (g->links[p]) cudaFree(g->links[p]);
@@ -242,7 +243,8 @@ void bpp_solve_opts_default(bpp_solve_opts* o) {
     o->max_outer = 50;
     o->use_x0 = 0;
     o->dagger = 0;
-    o->check_every = 16;
+    o->check_every = 4;
+    o->use_graph = 1;
 }
 
 int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs,
@@ -335,7 +337,10 @@ int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int re
 }
 
 int bpp_release_workspace(void) {
-    return guard("bpp_release_workspace", [&]() -> int { return release_workspace(); });
+    return guard("bpp_release_workspace", [&]() -> int {
+        drop_plans(nullptr);
+        return release_workspace();
+    });
 }
 
 }  // extern "C"

@@ -18,11 +18,14 @@ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.
 
 void RedBuf::ensure(int nblocks, int nsys, cudaStream_t st) {
     if (nblocks > cap_blocks) {
-        partials.alloc((size_t)nblocks * 4 * sizeof(double), st);
+        BPP_REQUIRE(!capturing(st), BPP_ERR_CUDA, "reduction buffer must be sized before graph capture");
+        if (persistent) partials.alloc_persistent((size_t)nblocks * 4 * sizeof(double));
+        else partials.alloc((size_t)nblocks * 4 * sizeof(double), st);
         cap_blocks = nblocks;
     }
     if (tickets.n < (size_t)MAXSYS * sizeof(unsigned)) {
-        tickets.alloc((size_t)MAXSYS * sizeof(unsigned), st);
+        if (persistent) tickets.alloc_persistent((size_t)MAXSYS * sizeof(unsigned));
+        else tickets.alloc((size_t)MAXSYS * sizeof(unsigned), st);
         BPP_CUDA(cudaMemsetAsync(tickets.p, 0, (size_t)MAXSYS * sizeof(unsigned), st));
     }
 }

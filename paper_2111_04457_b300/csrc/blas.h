@@ -31,8 +31,9 @@ struct KScal {
 // Workspace for the reductions of one batch.
 struct RedBuf {
     DevBuf partials;   // nblocks * 4 doubles
-    DevBuf tickets;    // nsys unsigned
+    DevBuf tickets;    // MAXSYS unsigned, self-resetting
     int cap_blocks = 0;
+    bool persistent = false;
     void ensure(int nblocks, int nsys, cudaStream_t st);
 };
 

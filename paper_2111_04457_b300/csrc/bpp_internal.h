@@ -338,8 +338,11 @@ __host__ __device__ __forceinline__ SpinorView sys_view(char* base, const SysDes
 }
 
 // ----------------------------------------------------------------------------- runtime
-// Counts every kernel launch of the library (bpp_launch_count).
+// Counts every kernel launch of the library (bpp_launch_count); launches made
+// while the calling thread captures a CUDA graph are not counted (the graph's
+// executions are counted instead).
 void count_launch(int64_t n = 1);
+void set_capturing(bool on);
 // True while `s` is being captured into a CUDA graph.
 bool capturing(cudaStream_t s);
 // Chooses the block size for a launch identified by `key` (kernel + shape).
@@ -360,13 +363,17 @@ struct ProfScope {
 };
 
 // Stream-ordered device scratch from the CUDA memory pool (cached by the pool).
+// With persistent = true the block comes from cudaMalloc (for long-lived
+// solver plans that outlive the caller's stream).
 struct DevBuf {
     void* p = nullptr;
     size_t n = 0;
     cudaStream_t s = nullptr;
+    bool persistent = false;
     DevBuf() = default;
     DevBuf(size_t bytes, cudaStream_t st) { alloc(bytes, st); }
     void alloc(size_t bytes, cudaStream_t st);
+    void alloc_persistent(size_t bytes);
     void release();
     ~DevBuf() { release(); }
     DevBuf(const DevBuf&) = delete;

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value) k_hop(HopParams hp) {
     using real = typename PT<P>::real;
     int s, tile;
     map_block(hp.map, s, tile);
+    if (hp.done && hp.done[s * hp.done_stride]) return;
     const SysDesc& d = hp.sys[s];
     const Geom g = d.g;
     const int i = tile * blockDim.x + threadIdx.x;
@@ -204,8 +205,11 @@ double hop_bytes_per_site(int prec, int mode) {
 }
 
 template <int P, bool DAG, int MODE>
-static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* out, char* y, cudaStream_t st) {
+static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* out, char* y, cudaStream_t st,
+                     const int* done, int done_stride) {
     HopParams hp;
+    hp.done = done;
+    hp.done_stride = done_stride;
     hp.sys = b.dev();
     hp.parity = parity;
     hp.in = in;
@@ -230,29 +234,29 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
 
 template <int P, bool DAG>
 static void launch_mode(const Batch& b, int parity, int mode, double a_sign, char* in, char* out, char* y,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* dn, int ds) {
     switch (mode) {
-        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st); break;
-        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st); break;
-        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st); break;
-        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st); break;
-        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st); break;
+        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st, dn, ds); break;
+        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds); break;
+        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds); break;
+        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st, dn, ds); break;
+        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds); break;
         default: throw Error(BPP_ERR_INVALID_ARG, "bad hopping mode");
     }
 }
 
 void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
-         cudaStream_t st) {
+         cudaStream_t st, const int* dn, int ds) {
     BPP_REQUIRE(in != out, BPP_ERR_INVALID_ARG, "hopping term: output aliases input");
     if (b.prec == P64) {
-        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st)
-            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st);
+        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
+            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
     } else if (b.prec == P32) {
-        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st)
-            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st);
+        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
+            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
     } else {
-        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st)
-            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st);
+        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
+            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
     }
 }
 

@@ -20,11 +20,13 @@ struct HopParams {
     char* out;         // batch vector on parity
     char* y;           // batch vector on parity (xpay operand) or null
     double a_sign;     // a = a_sign * kappa of the system
+    const int* done;   // optional per-system "converged" flags (skip those systems)
+    int done_stride;   // ints between consecutive flags
 };
 
 // out_p = epilogue(a * hop_{p,1-p} in) over every system of the batch.
 void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
-         cudaStream_t st);
+         cudaStream_t st, const int* done = nullptr, int done_stride = 0);
 double hop_bytes_per_site(int prec, int mode);
 
 // ----------------------------------------------------------------------------- layout

@@ -14,8 +14,13 @@
 namespace bpp {
 
 static std::atomic<int64_t> g_launches{0};
+static thread_local bool t_capturing = false;
 
-void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_capturing(bool on) { t_capturing = on; }
+
+void count_launch(int64_t n) {
+    if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 
 bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -150,10 +155,22 @@ void DevBuf::alloc(size_t bytes, cudaStream_t st) {
     BPP_CUDA(cudaMallocAsync(&p, bytes, st));
 }
 
+void DevBuf::alloc_persistent(size_t bytes) {
+    release();
+    persistent = true;
+    n = bytes;
+    if (bytes == 0) return;
+    BPP_CUDA(cudaMalloc(&p, bytes));
+}
+
 void DevBuf::release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+        if (persistent) cudaFree(p);
+        else cudaFreeAsync(p, s);
+    }
     p = nullptr;
     n = 0;
+    persistent = false;
 }
 
 int release_workspace() {

@@ -15,8 +15,11 @@
 // Mhat^dag Mhat with Mhat^dag = gamma5 Mhat gamma5) on the Schur system, over a
 // batch of systems (right-hand sides and/or lattices) that every launch covers;
 // the host only reads the per-system scalars every check_every iterations.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "blas.h"
@@ -37,8 +40,6 @@ struct Vec {
     char* p() const { return buf.as<char>(); }
 };
 
-static void make_vec(Vec& v, const Batch& bt, cudaStream_t st) { v.buf.alloc(bt.vec_bytes, st); }
-
 static void read_scalars(const DevBuf& d, std::vector<KScal>& h, cudaStream_t st) {
     BPP_CUDA(cudaMemcpyAsync(h.data(), d.p, h.size() * sizeof(KScal), cudaMemcpyDeviceToHost, st));
     BPP_CUDA(cudaStreamSynchronize(st));
@@ -47,55 +48,254 @@ static void write_scalars(DevBuf& d, const std::vector<KScal>& h, cudaStream_t s
     BPP_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(KScal), cudaMemcpyHostToDevice, st));
 }
 
-// Inner Krylov solve Mhat e = rhs on batch bP; returns per-system iterations.
-static void inner_solve(const Batch& bP, bool clover, int solver, Vec* w, DevBuf& dsc, std::vector<KScal>& hsc,
-                        RedBuf& rb, int check_every, int max_iter, cudaStream_t st) {
-    KScal* sc = dsc.as<KScal>();
-    // every active system advances one iteration per pass, so this many chunks
-    // always suffice; the cap only guards the host loop
-    const int max_chunks = max_iter / check_every + 2;
-    int chunks = 0;
-    BlasVecs v;
-    if (solver == BPP_BICGSTAB) {
-        v.b = w[0].p(); v.x = w[1].p(); v.r = w[2].p(); v.rhat = w[3].p(); v.p = w[4].p();
-        v.v = w[5].p(); v.s = w[6].p(); v.t = w[7].p();
-        char* tmp = w[8].p();
-        blas(bP, B_INIT_BICG, v, sc, rb, st);
-        for (;;) {
-            for (int k = 0; k < check_every; ++k) {
-                schur(bP, clover, 0, v.p, v.v, tmp, st);
-                blas(bP, B_ALPHA, v, sc, rb, st);
-                blas(bP, B_S, v, sc, rb, st);
-                schur(bP, clover, 0, v.s, v.t, tmp, st);
-                blas(bP, B_OMEGA, v, sc, rb, st);
-                blas(bP, B_XR, v, sc, rb, st);
-                blas(bP, B_P, v, sc, rb, st);
-            }
-            read_scalars(dsc, hsc, st);
-            bool all = true;
-            for (auto& k : hsc) all = all && k.done;
-            if (all || ++chunks >= max_chunks) break;
-        }
-    } else {
-        v.b = w[0].p(); v.x = w[1].p(); v.r = w[2].p(); v.z = w[3].p(); v.p = w[4].p(); v.w = w[5].p();
-        char* tmp = w[8].p();
-        blas(bP, B_CG_INIT, v, sc, rb, st);
-        schur(bP, clover, 1, v.r, v.z, tmp, st);
-        blas(bP, B_CG_PZ, v, sc, rb, st);
-        for (;;) {
-            for (int k = 0; k < check_every; ++k) {
-                schur(bP, clover, 0, v.p, v.w, tmp, st);
-                blas(bP, B_CG_ALPHA, v, sc, rb, st);
-                blas(bP, B_CG_XR, v, sc, rb, st);
-                schur(bP, clover, 1, v.r, v.z, tmp, st);
-                blas(bP, B_CG_BETA, v, sc, rb, st);
-            }
-            read_scalars(dsc, hsc, st);
-            bool all = true;
-            for (auto& k : hsc) all = all && k.done;
-            if (all || ++chunks >= max_chunks) break;
-        }
+// Loop control of the graph-captured inner solve: keep iterating while any
+// system is active, at most max_loops times.
+__global__ void k_loop_ctl(const KScal* sc, int n, int* loops, int max_loops, cudaGraphConditionalHandle h) {
+    bool active = false;
+    for (int s = threadIdx.x; s < n; s += 32) active = active || !sc[s].done;
+    active = __any_sync(0xffffffffu, active);
+    if (threadIdx.x == 0) {
+        const int l = *loops + 1;
+        *loops = l;
+        cudaGraphSetConditional(h, (active && l < max_loops) ? 1u : 0u);
     }
+}
+
+// Everything one configuration of systems needs, kept across calls so that
+// repeated solves (a propagator's 12 sources, a benchmark loop) reuse the
+// vectors, the reduction buffers and the instantiated inner-solve graph.
+struct Plan {
+    std::vector<const Gauge*> G;
+    std::vector<double> kappa;
+    bool clover = false;
+    int prec = P32, solver = BPP_BICGSTAB;
+    Batch b64, bP;
+    Vec be, bo, bhat, xe, xo, r, tmpo;
+    Vec w[9];
+    RedBuf rb;
+    DevBuf d64, dP, dloops;
+    std::vector<KScal> h64, hP;
+    bool warmed = false;                 // one eager inner solve ran (autotuner populated)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_max_iter = -1;
+    int body_kernels = 0;
+    size_t bytes = 0;
+    uint64_t last_use = 0;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+static std::mutex g_plan_mu;
+static std::vector<std::unique_ptr<Plan>> g_plans;
+static uint64_t g_plan_clock = 0;
+static const size_t PLAN_BUDGET = (size_t)48 << 30;
+static const size_t MAX_PLANS = 4;
+
+static void alloc_vec(Plan& pl, Vec& v, const Batch& b) {
+    v.buf.alloc_persistent(b.vec_bytes);
+    pl.bytes += b.vec_bytes;
+}
+
+static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<double>& kappa, bool clover, int prec,
+                      int solver, cudaStream_t st) {
+    ++g_plan_clock;
+    for (auto& p : g_plans)
+        if (p->G == G && p->kappa == kappa && p->clover == clover && p->prec == prec && p->solver == solver) {
+            p->last_use = g_plan_clock;
+            return *p;
+        }
+    std::unique_ptr<Plan> pl(new Plan());
+    pl->G = G;
+    pl->kappa = kappa;
+    pl->clover = clover;
+    pl->prec = prec;
+    pl->solver = solver;
+    pl->b64.prec = P64;
+    pl->bP.prec = prec;
+    for (size_t s = 0; s < G.size(); ++s) {
+        batch_add(pl->b64, *G[s], kappa[s], clover);
+        batch_add(pl->bP, *G[s], kappa[s], clover);
+    }
+    // evict least recently used plans beyond the count or byte budget
+    const size_t need = 7 * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes;
+    for (;;) {
+        size_t total = need;
+        for (auto& p : g_plans) total += p->bytes;
+        if (g_plans.empty() || (g_plans.size() < MAX_PLANS && total <= PLAN_BUDGET)) break;
+        size_t lru = 0;
+        for (size_t i = 1; i < g_plans.size(); ++i)
+            if (g_plans[i]->last_use < g_plans[lru]->last_use) lru = i;
+        BPP_CUDA(cudaDeviceSynchronize());
+        g_plans.erase(g_plans.begin() + lru);
+    }
+    pl->b64.dsys.persistent = true;
+    pl->bP.dsys.persistent = true;
+    pl->b64.dsys.alloc_persistent(pl->b64.sys.size() * sizeof(SysDesc));
+    pl->bP.dsys.alloc_persistent(pl->bP.sys.size() * sizeof(SysDesc));
+    BPP_CUDA(cudaMemcpy(pl->b64.dsys.p, pl->b64.sys.data(), pl->b64.sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    BPP_CUDA(cudaMemcpy(pl->bP.dsys.p, pl->bP.sys.data(), pl->bP.sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    for (Vec* v : {&pl->be, &pl->bo, &pl->bhat, &pl->xe, &pl->xo, &pl->r, &pl->tmpo}) alloc_vec(*pl, *v, pl->b64);
+    for (auto& v : pl->w) alloc_vec(*pl, v, pl->bP);
+    const int n = (int)G.size();
+    pl->rb.persistent = true;
+    pl->d64.alloc_persistent(n * sizeof(KScal));
+    pl->dP.alloc_persistent(n * sizeof(KScal));
+    pl->dloops.alloc_persistent(sizeof(int));
+    BPP_CUDA(cudaMemset(pl->d64.p, 0, n * sizeof(KScal)));
+    BPP_CUDA(cudaMemset(pl->dP.p, 0, n * sizeof(KScal)));
+    pl->h64.resize(n);
+    pl->hP.resize(n);
+    pl->last_use = g_plan_clock;
+    (void)st;
+    g_plans.push_back(std::move(pl));
+    return *g_plans.back();
+}
+
+void drop_plans(const Gauge* G) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    bool any = false;
+    for (auto& p : g_plans)
+        for (auto* g : p->G) any = any || G == nullptr || g == G;
+    if (!any) return;
+    cudaDeviceSynchronize();
+    g_plans.erase(std::remove_if(g_plans.begin(), g_plans.end(),
+                                 [&](const std::unique_ptr<Plan>& p) {
+                                     if (G == nullptr) return true;
+                                     for (auto* g : p->G)
+                                         if (g == G) return true;
+                                     return false;
+                                 }),
+                  g_plans.end());
+}
+
+// One iteration of the inner Krylov method on every active system.
+static void inner_iteration(Plan& pl, const BlasVecs& v, char* tmp, cudaStream_t st) {
+    const Batch& bP = pl.bP;
+    KScal* sc = pl.dP.as<KScal>();
+    const int* done = &sc[0].done;
+    const int ds = (int)(sizeof(KScal) / sizeof(int));
+    auto schur_s = [&](int dag, char* in, char* out) {
+        hop(bP, 1, dag, pl.clover ? HOP_INV : HOP_PLAIN, -1.0, in, tmp, nullptr, st, done, ds);
+        hop(bP, 0, dag, pl.clover ? HOP_CLOV_XPAY : HOP_XPAY, +1.0, tmp, out, in, st, done, ds);
+    };
+    if (pl.solver == BPP_BICGSTAB) {
+        schur_s(0, v.p, v.v);
+        blas(bP, B_ALPHA, v, sc, pl.rb, st);
+        blas(bP, B_S, v, sc, pl.rb, st);
+        schur_s(0, v.s, v.t);
+        blas(bP, B_OMEGA, v, sc, pl.rb, st);
+        blas(bP, B_XR, v, sc, pl.rb, st);
+        blas(bP, B_P, v, sc, pl.rb, st);
+    } else {
+        schur_s(0, v.p, v.w);
+        blas(bP, B_CG_ALPHA, v, sc, pl.rb, st);
+        blas(bP, B_CG_XR, v, sc, pl.rb, st);
+        schur_s(1, v.r, v.z);
+        blas(bP, B_CG_BETA, v, sc, pl.rb, st);
+    }
+}
+
+static BlasVecs inner_vecs(Plan& pl) {
+    BlasVecs v;
+    if (pl.solver == BPP_BICGSTAB) {
+        v.b = pl.w[0].p(); v.x = pl.w[1].p(); v.r = pl.w[2].p(); v.rhat = pl.w[3].p(); v.p = pl.w[4].p();
+        v.v = pl.w[5].p(); v.s = pl.w[6].p(); v.t = pl.w[7].p();
+    } else {
+        v.b = pl.w[0].p(); v.x = pl.w[1].p(); v.r = pl.w[2].p(); v.z = pl.w[3].p(); v.p = pl.w[4].p();
+        v.w = pl.w[5].p();
+    }
+    return v;
+}
+
+static void inner_init(Plan& pl, const BlasVecs& v, char* tmp, cudaStream_t st) {
+    KScal* sc = pl.dP.as<KScal>();
+    if (pl.solver == BPP_BICGSTAB) {
+        blas(pl.bP, B_INIT_BICG, v, sc, pl.rb, st);
+    } else {
+        blas(pl.bP, B_CG_INIT, v, sc, pl.rb, st);
+        schur(pl.bP, pl.clover, 1, v.r, v.z, tmp, st);
+        blas(pl.bP, B_CG_PZ, v, sc, pl.rb, st);
+    }
+}
+
+static int body_kernel_count(const Plan& pl) {
+    // hop launches + blas launches per iteration (+ the loop control kernel)
+    return pl.solver == BPP_BICGSTAB ? 4 + 5 + 1 : 4 + 4 + 1;
+}
+
+// Captures one iteration plus the loop control into the body of a while node.
+static void build_graph(Plan& pl, int max_iter) {
+    if (pl.exec) { cudaGraphExecDestroy(pl.exec); pl.exec = nullptr; }
+    if (pl.graph) { cudaGraphDestroy(pl.graph); pl.graph = nullptr; }
+    cudaStream_t cs;
+    BPP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    try {
+        BPP_CUDA(cudaGraphCreate(&pl.graph, 0));
+        cudaGraphConditionalHandle handle;
+        BPP_CUDA(cudaGraphConditionalHandleCreate(&handle, pl.graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        BPP_CUDA(cudaGraphAddNode(&node, pl.graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        BPP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        set_capturing(true);
+        try {
+            BlasVecs v = inner_vecs(pl);
+            inner_iteration(pl, v, pl.w[8].p(), cs);
+            k_loop_ctl<<<1, 32, 0, cs>>>(pl.dP.as<KScal>(), pl.bP.nsys(), pl.dloops.as<int>(), max_iter + 1, handle);
+            BPP_CHECK_LAUNCH();
+        } catch (...) {
+            set_capturing(false);
+            cudaGraph_t dummy;
+            cudaStreamEndCapture(cs, &dummy);
+            throw;
+        }
+        set_capturing(false);
+        cudaGraph_t captured;
+        BPP_CUDA(cudaStreamEndCapture(cs, &captured));
+        BPP_CUDA(cudaGraphInstantiate(&pl.exec, pl.graph, 0));
+        pl.graph_max_iter = max_iter;
+        pl.body_kernels = body_kernel_count(pl);
+    } catch (...) {
+        cudaStreamDestroy(cs);
+        throw;
+    }
+    BPP_CUDA(cudaStreamDestroy(cs));
+}
+
+// Inner Krylov solve Mhat e = rhs (in w[0]) on batch bP into w[1].
+static void inner_solve(Plan& pl, const bpp_solve_opts& o, cudaStream_t st) {
+    BlasVecs v = inner_vecs(pl);
+    char* tmp = pl.w[8].p();
+    inner_init(pl, v, tmp, st);
+    if (o.use_graph && pl.warmed) {
+        if (!pl.exec || pl.graph_max_iter != o.max_inner) build_graph(pl, o.max_inner);
+        BPP_CUDA(cudaMemsetAsync(pl.dloops.p, 0, sizeof(int), st));
+        BPP_CUDA(cudaGraphLaunch(pl.exec, st));
+        int loops = 0;
+        BPP_CUDA(cudaMemcpyAsync(&loops, pl.dloops.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        read_scalars(pl.dP, pl.hP, st);
+        count_launch((int64_t)loops * pl.body_kernels);
+        return;
+    }
+    // eager: host checks every check_every iterations; the hopping kernels and
+    // the vector updates skip systems that have converged
+    const int max_chunks = o.max_inner / o.check_every + 2;
+    for (int chunk = 0; chunk < max_chunks; ++chunk) {
+        for (int k = 0; k < o.check_every; ++k) inner_iteration(pl, v, tmp, st);
+        read_scalars(pl.dP, pl.hP, st);
+        bool all = true;
+        for (auto& k : pl.hP) all = all && k.done;
+        if (all) break;
+    }
+    pl.warmed = true;
 }
 
 int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& kappa, bool clover,
@@ -109,63 +309,47 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     BPP_REQUIRE(o.inner_prec >= BPP_F64 && o.inner_prec <= BPP_F16, BPP_ERR_INVALID_ARG, "unknown inner precision");
     BPP_REQUIRE(o.max_inner > 0 && o.max_outer > 0 && o.check_every > 0, BPP_ERR_INVALID_ARG, "iteration caps must be positive");
 
-    Batch b64, bP;
-    b64.prec = P64;
-    bP.prec = o.inner_prec;
-    for (int s = 0; s < n; ++s) {
-        batch_add(b64, *G[s], kappa[s], clover);
-        batch_add(bP, *G[s], kappa[s], clover);
-    }
-    b64.upload(st);
-    bP.upload(st);
-
-    // FP64 vectors: b_e, b_o, bhat, x_e, x_o, r (even), tmp_o, De/Do scratch
-    Vec be, bo, bhat, xe, xo, r, tmpo;
-    for (Vec* v : {&be, &bo, &bhat, &xe, &xo, &r, &tmpo}) make_vec(*v, b64, st);
-    // inner vectors
-    Vec w[9];
-    for (auto& v : w) make_vec(v, bP, st);
-    RedBuf rb;
-    DevBuf d64(n * sizeof(KScal), st), dP(n * sizeof(KScal), st);
-    std::vector<KScal> h64(n), hP(n);
-    BPP_CUDA(cudaMemsetAsync(d64.p, 0, n * sizeof(KScal), st));
-    BPP_CUDA(cudaMemsetAsync(dP.p, 0, n * sizeof(KScal), st));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, st);
+    const Batch& b64 = pl.b64;
+    const Batch& bP = pl.bP;
+    KScal* sc64 = pl.d64.as<KScal>();
+    std::vector<KScal>& h64 = pl.h64;
+    std::vector<KScal>& hP = pl.hP;
+    pl.rb.ensure(1, n, st);   // tickets
 
     // b -> even/odd FP64 (gamma5 b for the adjoint solve)
-    for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, b_canon[s], 1, 0, be.p(), bo.p(), o.dagger ? 1 : 0, st);
+    for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, b_canon[s], 1, 0, pl.be.p(), pl.bo.p(), o.dagger ? 1 : 0, st);
     const int dag = 0;
     // bhat = b_e + kappa H_eo A_oo^-1 b_o
     if (clover) {
-        clover_apply(b64, 1, 1, bo.p(), tmpo.p(), st);
-        hop(b64, 0, dag, HOP_XPAY, +1.0, tmpo.p(), bhat.p(), be.p(), st);
+        clover_apply(b64, 1, 1, pl.bo.p(), pl.tmpo.p(), st);
+        hop(b64, 0, dag, HOP_XPAY, +1.0, pl.tmpo.p(), pl.bhat.p(), pl.be.p(), st);
     } else {
-        hop(b64, 0, dag, HOP_XPAY, +1.0, bo.p(), bhat.p(), be.p(), st);
+        hop(b64, 0, dag, HOP_XPAY, +1.0, pl.bo.p(), pl.bhat.p(), pl.be.p(), st);
     }
-    // norms: ||b||^2 = ||b_e||^2 + ||b_o||^2, ||bhat||^2
-    std::vector<double> bnorm2(n), bhat2(n);
+    // norms: ||b||^2 = ||b_e||^2 + ||b_o||^2
+    std::vector<double> bnorm2(n);
     {
         BlasVecs v;
-        v.x = be.p();
-        blas(b64, B_NORM2, v, d64.as<KScal>(), rb, st);
-        read_scalars(d64, h64, st);
+        v.x = pl.be.p();
+        blas(b64, B_NORM2, v, sc64, pl.rb, st);
+        read_scalars(pl.d64, h64, st);
         for (int s = 0; s < n; ++s) bnorm2[s] = h64[s].bb;
-        v.x = bo.p();
-        blas(b64, B_NORM2, v, d64.as<KScal>(), rb, st);
-        read_scalars(d64, h64, st);
+        v.x = pl.bo.p();
+        blas(b64, B_NORM2, v, sc64, pl.rb, st);
+        read_scalars(pl.d64, h64, st);
         for (int s = 0; s < n; ++s) bnorm2[s] += h64[s].bb;
-        v.x = bhat.p();
-        blas(b64, B_NORM2, v, d64.as<KScal>(), rb, st);
-        read_scalars(d64, h64, st);
-        for (int s = 0; s < n; ++s) bhat2[s] = h64[s].bb;
     }
     for (int s = 0; s < n; ++s)
-        BPP_REQUIRE(std::isfinite(bnorm2[s]) && std::isfinite(bhat2[s]), BPP_ERR_NONFINITE, "non-finite right-hand side");
+        BPP_REQUIRE(std::isfinite(bnorm2[s]), BPP_ERR_NONFINITE, "non-finite right-hand side");
 
     // initial guess
+    bool x_zero = !o.use_x0;
     if (o.use_x0) {
-        for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, x_canon[s], 1, 0, xe.p(), xo.p(), o.dagger ? 1 : 0, st);
+        for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
     } else {
-        BPP_CUDA(cudaMemsetAsync(xe.p(), 0, b64.vec_bytes, st));
+        BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
     }
 
     // Schur-residual target per system: ||bhat - Mhat x|| <= target * ||b||
@@ -175,10 +359,15 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     const int max_checks = 4;
     for (int check = 0; check < max_checks; ++check) {
         for (int it = 0; it < o.max_outer; ++it) {
-            // r = bhat - Mhat x
-            schur(b64, clover, dag, xe.p(), r.p(), tmpo.p(), st);
-            outer_residual(b64, bhat.p(), r.p(), d64.as<KScal>(), rb, st);
-            read_scalars(d64, h64, st);
+            // r = bhat - Mhat x (x = 0: r = bhat without a matrix application)
+            if (x_zero) {
+                BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
+                x_zero = false;
+            } else {
+                schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
+            }
+            outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+            read_scalars(pl.d64, h64, st);
             bool all = true;
             for (int s = 0; s < n; ++s) {
                 if (!std::isfinite(h64[s].rr)) { status[s] = BPP_ERR_NONFINITE; h64[s].scale = 0.0; continue; }
@@ -187,36 +376,35 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                 all = false;
             }
             if (all) break;
-            write_scalars(d64, h64, st);
+            write_scalars(pl.d64, h64, st);
             // inner solve of Mhat e = r/||r||
             for (int s = 0; s < n; ++s) {
                 KScal k{};
                 const double rn = std::sqrt(std::max(h64[s].rr, 0.0));
-                double itol = o.inner_tol;
-                if (bP.prec == P64 || itol <= 0.0) itol = 0.5 * target[s] * std::sqrt(bnorm2[s]) / std::max(rn, 1e-300);
-                itol = std::max(itol, 0.5 * target[s] * std::sqrt(bnorm2[s]) / std::max(rn, 1e-300));
+                const double need = 0.5 * target[s] * std::sqrt(bnorm2[s]) / std::max(rn, 1e-300);
+                double itol = (bP.prec == P64 || o.inner_tol <= 0.0) ? need : std::max(o.inner_tol, need);
                 k.tol2 = itol * itol;
                 k.max_iter = o.max_inner;
                 hP[s] = k;
                 if (h64[s].scale > 0.0) outer[s] += 1;
             }
-            write_scalars(dP, hP, st);
-            outer_downcast(b64, bP, r.p(), w[0].p(), d64.as<KScal>(), st);
-            inner_solve(bP, clover, o.solver, w, dP, hP, rb, o.check_every, o.max_inner, st);
+            write_scalars(pl.dP, hP, st);
+            outer_downcast(b64, bP, pl.r.p(), pl.w[0].p(), sc64, st);
+            inner_solve(pl, o, st);
             for (int s = 0; s < n; ++s) inner_it[s] += h64[s].scale > 0.0 ? hP[s].iter : 0;
-            outer_accumulate(b64, bP, xe.p(), w[1].p(), d64.as<KScal>(), st);
+            outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st);
         }
         // x_o = A_oo^-1 (b_o + kappa H_oe x_e)
-        hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, xe.p(), xo.p(), bo.p(), st);
+        hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), st);
         // true residual with the full FP64 D: De = A_ee x_e - kappa H_eo x_o, Do = A_oo x_o - kappa H_oe x_e
-        hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, xo.p(), r.p(), xe.p(), st);
-        outer_residual(b64, be.p(), r.p(), d64.as<KScal>(), rb, st);
-        read_scalars(d64, h64, st);
+        hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xo.p(), pl.r.p(), pl.xe.p(), st);
+        outer_residual(b64, pl.be.p(), pl.r.p(), sc64, pl.rb, st);
+        read_scalars(pl.d64, h64, st);
         std::vector<double> rr(n);
         for (int s = 0; s < n; ++s) rr[s] = h64[s].rr;
-        hop(b64, 1, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, xe.p(), tmpo.p(), xo.p(), st);
-        outer_residual(b64, bo.p(), tmpo.p(), d64.as<KScal>(), rb, st);
-        read_scalars(d64, h64, st);
+        hop(b64, 1, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xe.p(), pl.tmpo.p(), pl.xo.p(), st);
+        outer_residual(b64, pl.bo.p(), pl.tmpo.p(), sc64, pl.rb, st);
+        read_scalars(pl.d64, h64, st);
         bool again = false;
         for (int s = 0; s < n; ++s) {
             rr[s] += h64[s].rr;
@@ -230,7 +418,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         }
         if (!again) break;
     }
-    for (int s = 0; s < n; ++s) eo_to_full(b64, s, 1, xe.p(), xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st);
+    for (int s = 0; s < n; ++s) eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st);
     BPP_CUDA(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int rc = BPP_OK;

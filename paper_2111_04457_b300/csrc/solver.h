@@ -17,6 +17,9 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                 const std::vector<const void*>& b_canon, const std::vector<void*>& x_canon, double tol,
                 const bpp_solve_opts& o, bpp_solve_stats* stats, cudaStream_t st);
 
+// Releases cached solver plans that use gauge G (all plans for G == nullptr).
+void drop_plans(const Gauge* G);
+
 // Link gradient / projected force (see bpp_force).
 void force(const Gauge& G, const void* x, const void* lam, double kappa, void* dU, int project, cudaStream_t st);
 

@@ -1,0 +1,72 @@
+"""Batching (the 12 spin-colour sources of a propagator, Fig. 1; lattices of
+uneven sizes) and the graph-captured inner loop.  A system's result does not
+depend on the batch it runs in, nor on graph versus eager execution: the
+kernels, block-to-site maps of each system and reduction orders are the same,
+so results must be bit-identical."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import BC, gauge, lib, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def test_graph_equals_eager():
+    bpp = lib()
+    L = (6, 6, 6, 10)
+    g, U = gauge(L)
+    b = to_dev(synth.gaussian_spinor(L, seed=2))
+    for inner in [bpp.F32, bpp.F16, bpp.F64]:
+        xe, se = bpp.solve(g, b, 0.12, 0.0, TOL, bpp.solve_opts(inner_prec=inner, use_graph=False))
+        xg, sg = bpp.solve(g, b, 0.12, 0.0, TOL, bpp.solve_opts(inner_prec=inner, use_graph=True))
+        xg2, _ = bpp.solve(g, b, 0.12, 0.0, TOL, bpp.solve_opts(inner_prec=inner, use_graph=True))
+        assert torch.equal(xe, xg) and torch.equal(xg, xg2)
+        assert se[0]["inner_iters"] == sg[0]["inner_iters"]
+
+
+def test_uneven_batch_matches_single():
+    bpp = lib()
+    lats = [(4, 4, 4, 4), (6, 6, 6, 6), (4, 4, 4, 8), (8, 4, 4, 6)]
+    kappas = synth.uniform_kappas(len(lats))
+    gs, Us, bs = [], [], []
+    for i, L in enumerate(lats):
+        g, U = gauge(L, seed=1 + i)
+        gs.append(g)
+        Us.append(U)
+        bs.append(to_dev(synth.gaussian_spinor(L, seed=2 + i)))
+    for inner in [bpp.F32, bpp.F16]:
+        opts = bpp.solve_opts(inner_prec=inner)
+        xs, st = bpp.solve_batch(gs, bs, kappas, TOL, opts)
+        for i, L in enumerate(lats):
+            x1, s1 = bpp.solve(gs[i], bs[i], kappas[i], 0.0, TOL, opts)
+            assert torch.equal(xs[i], x1), (L, inner)
+            assert st[i]["inner_iters"] == s1[0]["inner_iters"]
+            res = oracle.true_residual(Us[i], to_np(bs[i]), to_np(xs[i]), kappas[i], L, BC)
+            assert res <= TOL
+
+
+def test_twelve_sources_match_single():
+    bpp = lib()
+    L = (4, 4, 4, 8)
+    g, U = gauge(L)
+    b = np.stack([synth.point_source(L, idx) for idx in range(12)])
+    opts = bpp.solve_opts(inner_prec=bpp.F32)
+    x, st = bpp.solve(g, to_dev(b), 0.12, 0.0, TOL, opts)
+    for idx in [0, 5, 11]:
+        x1, _ = bpp.solve(g, to_dev(b[idx]), 0.12, 0.0, TOL, opts)
+        assert torch.equal(x[idx], x1[0] if x1.dim() == 4 else x1)
+
+
+def test_launch_count_grows():
+    bpp = lib()
+    L = (4, 4, 4, 4)
+    g, U = gauge(L)
+    b = to_dev(synth.gaussian_spinor(L, seed=2))
+    bpp.launch_count(reset=True)
+    bpp.solve(g, b, 0.12, 0.0, TOL)
+    n = bpp.launch_count()
+    assert n > 10
