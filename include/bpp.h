@@ -146,7 +146,8 @@ int bpp_dirac_apply(bpp_gauge U, const void* in, void* out, double kappa, double
 typedef struct {
     int solver;       /* bpp_solver: BPP_BICGSTAB or BPP_CGNR on the Schur system */
     int inner_prec;   /* bpp_prec of the inner Krylov solve */
-    double inner_tol; /* relative residual reduction per inner solve (ignored for F64) */
+    double inner_tol; /* relative residual reduction per inner solve (ignored for F64);
+                         <= 0 selects the default: 1e-6 for F32, 2e-3 for F16 */
     int max_inner;    /* iteration cap of one inner solve */
     int max_outer;    /* cap on defect-correction steps */
     int use_x0;       /* nonzero: x holds the initial guess on entry */
@@ -167,7 +168,7 @@ typedef struct {
     double seconds;     /* wall time of the whole call (same for every RHS) */
 } bpp_solve_stats;
 
-/* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 1e-5,
+/* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 0 (per precision),
  * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 1. */
 void bpp_solve_opts_default(bpp_solve_opts* opts);
 
@@ -217,6 +218,13 @@ int bpp_prof_enable(int enable);
  * precision prec: number of launches, total milliseconds, total algorithmic
  * bytes.  Synchronises the device. */
 int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int reset);
+
+/* Reads (and with reset != 0 clears) the work done by the even-odd hopping
+ * kernels of precision prec since load: launches and algorithmic bytes (per
+ * output site: 8 links + input and output spinor, + the xpay operand and
+ * clover blocks of fused epilogues).  Graph-executed iterations are credited
+ * per system for the iterations that system was active.  Does not synchronise. */
+int bpp_work_read(int prec, int64_t* launches, double* bytes, int reset);
 
 /* Releases cached device workspace (synchronises the device). */
 int bpp_release_workspace(void);

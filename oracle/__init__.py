@@ -84,6 +84,7 @@ def _load():
         p, d, i, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
         lib.oracle_dirac_apply.argtypes = [p, p, p, p, p, d, i, p, p, i64, p]
         lib.oracle_clover_field.argtypes = [p, p, p, d, d, p]
+        lib.oracle_clover_field_sites.argtypes = [p, p, p, d, d, p, i64, p]
         lib.oracle_clover_leaf.argtypes = [p, p, i, i, i64, p]
         lib.oracle_link_gradient.argtypes = [p, p, p, p, p, d, p]
         _lib = lib
@@ -140,6 +141,27 @@ def clover_field(U, kappa, csw, L):
     _load().oracle_clover_field(Lv.ctypes.data, GAMMA.ctypes.data, U.ctypes.data,
                                 float(kappa), float(csw), F.ctypes.data)
     return F
+
+
+def clover_field_sites(U, kappa, csw, L, sites):
+    """F(x) at the listed sites only, shape (len(sites),12,12)."""
+    sv = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    F = np.empty((len(sv), 12, 12), dtype=np.complex128)
+    U, Lv = _c128(U), _ivec(L)
+    _load().oracle_clover_field_sites(Lv.ctypes.data, GAMMA.ctypes.data, U.ctypes.data, float(kappa), float(csw),
+                                      F.ctypes.data, len(sv), sv.ctypes.data)
+    return F
+
+
+def apply_D_sites_clover(U, psi, kappa, L, csw, sites, bc=DEFAULT_BC, dagger=False):
+    """D psi (or D^dag psi) with the clover term at the listed sites only: the
+    hopping part from Eq. (1) plus F(x) psi(x) with F built at those sites."""
+    sv = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    out = apply_D(U, psi, kappa, L, bc, None, dagger, sites=sv)
+    if csw != 0.0:
+        F = clover_field_sites(U, kappa, csw, L, sv)
+        out = out + np.einsum("nij,nj->ni", F, psi[sv].reshape(len(sv), 12)).reshape(out.shape)
+    return out
 
 
 def link_gradient(x, lam, kappa, L, bc=DEFAULT_BC):

@@ -191,11 +191,13 @@ void oracle_clover_leaf(const int L[4], const cplx *U, int mu, int nu, int64_t s
 /* F(x) = i kappa c_SW sum_{mu<nu} sigma_{mu nu} (x) Fhat_{mu nu}(x), a 12x12
  * Hermitian matrix per site, with sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] and
  * Fhat = (Q - Q^dag)/8 from the clover leaf.  Links enter without boundary
- * signs.  Output F[(s*12 + i)*12 + j]. */
-void oracle_clover_field(const int L[4], const cplx *gamma, const cplx *U,
-                         double kappa, double csw, cplx *F)
+ * signs.  Output F[(k*12 + i)*12 + j] for the k-th listed site (all sites
+ * when sites == NULL). */
+void oracle_clover_field_sites(const int L[4], const cplx *gamma, const cplx *U, double kappa,
+                               double csw, cplx *F, int64_t nsites, const int64_t *sites)
 {
     const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    if (sites == NULL) nsites = V;
     cplx sigma[6][16];
     int pmu[6], pnu[6];
     int np = 0;
@@ -212,8 +214,9 @@ void oracle_clover_field(const int L[4], const cplx *gamma, const cplx *U,
             pmu[np] = mu; pnu[np] = nu; ++np;
         }
 #pragma omp parallel for schedule(static)
-    for (int64_t s = 0; s < V; ++s) {
-        cplx *f = &F[s * 144];
+    for (int64_t k = 0; k < nsites; ++k) {
+        const int64_t s = sites ? sites[k] : k;
+        cplx *f = &F[k * 144];
         for (int i = 0; i < 144; ++i) f[i] = 0.0;
         for (int p = 0; p < 6; ++p) {
             cplx Q[9], Fh[9];
@@ -227,6 +230,13 @@ void oracle_clover_field(const int L[4], const cplx *gamma, const cplx *U,
                             f[(sp * 3 + a) * 12 + tp * 3 + b] += I * kappa * csw * sigma[p][sp * 4 + tp] * Fh[a * 3 + b];
         }
     }
+}
+
+/* F(x) at every site (F[s*144 + ...]). */
+void oracle_clover_field(const int L[4], const cplx *gamma, const cplx *U,
+                         double kappa, double csw, cplx *F)
+{
+    oracle_clover_field_sites(L, gamma, U, kappa, csw, F, 0, NULL);
 }
 
 /* Unconstrained link gradient of L = Re<eta, D^{-1} b> for the Wilson hopping

@@ -82,6 +82,7 @@ _SIGS = {
     "bpp_launch_count": ([_i], _i64),
     "bpp_prof_enable": ([_i], _i),
     "bpp_prof_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), ctypes.POINTER(_d), _i], _i),
+    "bpp_work_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), _i], _i),
     "bpp_release_workspace": ([], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -135,6 +136,13 @@ def prof_read(prec: int, reset: bool = True):
     n, ms, by = _i64(), _d(), _d()
     _check(_lib.bpp_prof_read(prec, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), int(reset)))
     return n.value, ms.value, by.value
+
+
+def work_read(prec: int, reset: bool = True):
+    """(launches, algorithmic bytes) of the hopping kernels of precision prec, graph work included."""
+    n, by = _i64(), _d()
+    _check(_lib.bpp_work_read(prec, ctypes.byref(n), ctypes.byref(by), int(reset)))
+    return n.value, by.value
 
 
 def release_workspace():
@@ -261,8 +269,6 @@ def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000,
     o.inner_prec = inner_prec
     if inner_tol is not None:
         o.inner_tol = inner_tol
-    elif inner_prec == F16:
-        o.inner_tol = 5e-3
     o.max_inner = max_inner
     o.max_outer = max_outer
     o.dagger = int(dagger)

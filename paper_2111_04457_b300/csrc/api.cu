@@ -14,6 +14,7 @@ namespace bpp {
 int prof_enable(int on);
 int prof_read(int prec, int64_t* n, double* ms, double* bytes, int reset);
 int64_t launch_count(int reset);
+int work_read(int prec, int64_t* n, double* bytes, int reset);
 int release_workspace();
 }  // namespace bpp
 
@@ -238,7 +239,7 @@ void bpp_solve_opts_default(bpp_solve_opts* o) {
     if (!o) return;
     o->solver = BPP_BICGSTAB;
     o->inner_prec = BPP_F32;
-    o->inner_tol = 1e-5;
+    o->inner_tol = 0.0;
     o->max_inner = 20000;
     o->max_outer = 50;
     o->use_x0 = 0;
@@ -334,6 +335,10 @@ int bpp_prof_enable(int enable) { return prof_enable(enable); }
 
 int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int reset) {
     return guard("bpp_prof_read", [&]() -> int { return prof_read(prec, launches, ms, bytes, reset); });
+}
+
+int bpp_work_read(int prec, int64_t* launches, double* bytes, int reset) {
+    return guard("bpp_work_read", [&]() -> int { return work_read(prec, launches, bytes, reset); });
 }
 
 int bpp_release_workspace(void) {

@@ -343,6 +343,15 @@ __host__ __device__ __forceinline__ SpinorView sys_view(char* base, const SysDes
 // executions are counted instead).
 void count_launch(int64_t n = 1);
 void set_capturing(bool on);
+bool thread_capturing();
+// Algorithmic work of the hopping kernels (bpp_work_read): added per launch,
+// or, for launches recorded into a graph, accumulated per system into the
+// calling thread's capture record so the graph's executions can be credited.
+void add_hop_work(int prec, int64_t launches, double bytes);
+void capture_hop_work(int prec, int sys, double bytes);
+void capture_work_reset(int nsys);
+const std::vector<double>& capture_work_bytes();
+int capture_work_prec();
 // True while `s` is being captured into a CUDA graph.
 bool capturing(cudaStream_t s);
 // Chooses the block size for a launch identified by `key` (kernel + shape).

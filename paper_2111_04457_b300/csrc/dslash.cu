@@ -88,13 +88,87 @@ __device__ __forceinline__ void link_mul(const cx<real> U[9], const cx<real> h[6
         }
 }
 
+// Raw (undecoded) loads of one hop: the neighbour spinor and the link.
+template <int P> struct Raw;
+template <> struct Raw<P64> { double2 s[12]; double2 u[9]; };
+template <> struct Raw<P32> { float4 s[6]; float4 u[4]; float2 u8; };
+template <> struct Raw<P16> { uint4 s[3]; float sc; uint4 u[2]; unsigned u8; };
+
+__device__ __forceinline__ void load_raw(Raw<P64>& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
+    const double2* p = static_cast<const double2*>(in.data);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.s[k] = __ldg(p + k * in.stride + j);
+    const double2* q = static_cast<const double2*>(U.data);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r.u[k] = __ldcs(q + k * U.stride + ju);
+}
+__device__ __forceinline__ void load_raw(Raw<P32>& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
+    const float4* p = static_cast<const float4*>(in.data);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r.s[k] = __ldg(p + k * in.stride + j);
+    const float4* q = static_cast<const float4*>(U.data);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.u[k] = __ldcs(q + k * U.stride + ju);
+    r.u8 = __ldcs(reinterpret_cast<const float2*>(q + 4 * U.stride) + ju);
+}
+__device__ __forceinline__ void load_raw(Raw<P16>& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
+    const uint4* p = static_cast<const uint4*>(in.data);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.s[k] = __ldg(p + k * in.stride + j);
+    r.sc = __ldg(in.scale + j);
+    const uint4* q = static_cast<const uint4*>(U.data);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) r.u[k] = __ldcs(q + k * U.stride + ju);
+    r.u8 = __ldcs(reinterpret_cast<const unsigned*>(q + 2 * U.stride) + ju);
+}
+
+__device__ __forceinline__ void decode(const Raw<P64>& r, cx<double> psi[12], cx<double> u[9]) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) psi[k] = mkc(r.s[k].x, r.s[k].y);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = mkc(r.u[k].x, r.u[k].y);
+}
+__device__ __forceinline__ void decode(const Raw<P32>& r, cx<float> psi[12], cx<float> u[9]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        psi[2 * k] = mkc(r.s[k].x, r.s[k].y);
+        psi[2 * k + 1] = mkc(r.s[k].z, r.s[k].w);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        u[2 * k] = mkc(r.u[k].x, r.u[k].y);
+        u[2 * k + 1] = mkc(r.u[k].z, r.u[k].w);
+    }
+    u[8] = mkc(r.u8.x, r.u8.y);
+}
+__device__ __forceinline__ void decode(const Raw<P16>& r, cx<float> psi[12], cx<float> u[9]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float2 a = h2f(r.s[k].x), b = h2f(r.s[k].y), c = h2f(r.s[k].z), d = h2f(r.s[k].w);
+        psi[4 * k + 0] = mkc(a.x * r.sc, a.y * r.sc);
+        psi[4 * k + 1] = mkc(b.x * r.sc, b.y * r.sc);
+        psi[4 * k + 2] = mkc(c.x * r.sc, c.y * r.sc);
+        psi[4 * k + 3] = mkc(d.x * r.sc, d.y * r.sc);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float2 a = h2f(r.u[k].x), b = h2f(r.u[k].y), c = h2f(r.u[k].z), d = h2f(r.u[k].w);
+        u[4 * k + 0] = mkc(a.x, a.y);
+        u[4 * k + 1] = mkc(b.x, b.y);
+        u[4 * k + 2] = mkc(c.x, c.y);
+        u[4 * k + 3] = mkc(d.x, d.y);
+    }
+    const float2 a = h2f(r.u8);
+    u[8] = mkc(a.x, a.y);
+}
+
+// One hop term: decode, project with (1 + S gamma_MU), colour-multiply
+// (U or U^dag), reconstruct into acc.
 template <int P, int MU, int S, bool BACK>
-__device__ __forceinline__ void hop_dir(cx<typename PT<P>::real> acc[12], const SpinorView& in, int64_t j,
-                                        const LinkView& U, int64_t ju, bool flip) {
+__device__ __forceinline__ void hop_term(cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
     using real = typename PT<P>::real;
     cx<real> psi[12], h[6], g[6], u[9];
-    Access<P>::load_spinor(in, j, psi);
-    Access<P>::load_link(U, ju, u);
+    decode(raw, psi, u);
     project<MU, S>(psi, h);
     if (flip) {
 #pragma unroll
@@ -104,9 +178,37 @@ __device__ __forceinline__ void hop_dir(cx<typename PT<P>::real> acc[12], const 
     reconstruct<MU, S>(acc, g);
 }
 
+// Direction d = 2 mu + (0 forward, 1 backward); SF is the forward projector sign.
+template <int P, int SF>
+__device__ __forceinline__ void hop_term_d(int d, cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
+    switch (d) {
+        case 0: hop_term<P, 0, SF, false>(acc, raw, flip); break;
+        case 1: hop_term<P, 0, -SF, true>(acc, raw, flip); break;
+        case 2: hop_term<P, 1, SF, false>(acc, raw, flip); break;
+        case 3: hop_term<P, 1, -SF, true>(acc, raw, flip); break;
+        case 4: hop_term<P, 2, SF, false>(acc, raw, flip); break;
+        case 5: hop_term<P, 2, -SF, true>(acc, raw, flip); break;
+        case 6: hop_term<P, 3, SF, false>(acc, raw, flip); break;
+        default: hop_term<P, 3, -SF, true>(acc, raw, flip); break;
+    }
+}
+
+// Loads of the next hop are issued before the current one is computed for the
+// bandwidth-bound precisions (more bytes in flight per thread); FP64 is bound
+// by the FP64 pipe and keeps its registers for arithmetic.
+#ifndef BPP_HOP_PREFETCH
+#define BPP_HOP_PREFETCH 1
+#endif
+#ifndef BPP_HOP16_MAXT
+#define BPP_HOP16_MAXT 512
+#endif
+template <int P> struct HopPrefetch { static constexpr bool value = BPP_HOP_PREFETCH != 0; };
+template <> struct HopPrefetch<P64> { static constexpr bool value = false; };
+
 // FP64 needs more registers per thread than a 512-thread block allows.
 template <int P> struct HopMaxThreads { static constexpr int value = 512; };
 template <> struct HopMaxThreads<P64> { static constexpr int value = 256; };
+template <> struct HopMaxThreads<P16> { static constexpr int value = BPP_HOP16_MAXT; };
 
 template <int P, bool DAG, int MODE>
 __global__ void __launch_bounds__(HopMaxThreads<P>::value) k_hop(HopParams hp) {
@@ -129,42 +231,64 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value) k_hop(HopParams hp) {
     const int x1 = 2 * x1h + ((p + x2 + x3 + x4) & 1);
 
     const SpinorView in = sys_view<P>(hp.in, d);
+    // neighbour half-lattice index, link index and boundary flip of the 8 hops
+    int jn[8];
+    bool flip[8];
+    {
+        const bool wf = x1 == g.L[0] - 1, wb = x1 == 0;
+        jn[0] = ((wf ? 0 : x1 + 1) >> 1) + g.Lh * r;
+        jn[1] = ((wb ? g.L[0] - 1 : x1 - 1) >> 1) + g.Lh * r;
+        flip[0] = wf && g.bc[0] < 0;
+        flip[1] = wb && g.bc[0] < 0;
+    }
+    {
+        const bool wf = x2 == g.L[1] - 1, wb = x2 == 0;
+        jn[2] = x1h + g.Lh * (wf ? r - (g.L[1] - 1) : r + 1);
+        jn[3] = x1h + g.Lh * (wb ? r + (g.L[1] - 1) : r - 1);
+        flip[2] = wf && g.bc[1] < 0;
+        flip[3] = wb && g.bc[1] < 0;
+    }
+    {
+        const int st = g.L[1];
+        const bool wf = x3 == g.L[2] - 1, wb = x3 == 0;
+        jn[4] = x1h + g.Lh * (wf ? r - (g.L[2] - 1) * st : r + st);
+        jn[5] = x1h + g.Lh * (wb ? r + (g.L[2] - 1) * st : r - st);
+        flip[4] = wf && g.bc[2] < 0;
+        flip[5] = wb && g.bc[2] < 0;
+    }
+    {
+        const int st = g.L[1] * g.L[2];
+        const bool wf = x4 == g.L[3] - 1, wb = x4 == 0;
+        jn[6] = x1h + g.Lh * (wf ? r - (g.L[3] - 1) * st : r + st);
+        jn[7] = x1h + g.Lh * (wb ? r + (g.L[3] - 1) * st : r - st);
+        flip[6] = wf && g.bc[3] < 0;
+        flip[7] = wb && g.bc[3] < 0;
+    }
+    int ju[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ju[k] = (k & 1) ? jn[k] : i;   // forward: U_mu(x); backward: U_mu(x - mu)
+
     cx<real> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = mkc<real>(0, 0);
 
-    constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
-    constexpr int SB = -SF;             // backward projector
-    // mu = 0 (x1): neighbours stay in the same row r
-    {
-        const bool wf = x1 == g.L[0] - 1, wb = x1 == 0;
-        const int jf = ((wf ? 0 : x1 + 1) >> 1) + g.Lh * r;
-        const int jb = ((wb ? g.L[0] - 1 : x1 - 1) >> 1) + g.Lh * r;
-        hop_dir<P, 0, SF, false>(acc, in, jf, d.U[p][0], i, wf && g.bc[0] < 0);
-        hop_dir<P, 0, SB, true>(acc, in, jb, d.U[q][0], jb, wb && g.bc[0] < 0);
-    }
-    {   // mu = 1 (x2)
-        const bool wf = x2 == g.L[1] - 1, wb = x2 == 0;
-        const int jf = x1h + g.Lh * (wf ? r - (g.L[1] - 1) : r + 1);
-        const int jb = x1h + g.Lh * (wb ? r + (g.L[1] - 1) : r - 1);
-        hop_dir<P, 1, SF, false>(acc, in, jf, d.U[p][1], i, wf && g.bc[1] < 0);
-        hop_dir<P, 1, SB, true>(acc, in, jb, d.U[q][1], jb, wb && g.bc[1] < 0);
-    }
-    {   // mu = 2 (x3)
-        const int st = g.L[1];
-        const bool wf = x3 == g.L[2] - 1, wb = x3 == 0;
-        const int jf = x1h + g.Lh * (wf ? r - (g.L[2] - 1) * st : r + st);
-        const int jb = x1h + g.Lh * (wb ? r + (g.L[2] - 1) * st : r - st);
-        hop_dir<P, 2, SF, false>(acc, in, jf, d.U[p][2], i, wf && g.bc[2] < 0);
-        hop_dir<P, 2, SB, true>(acc, in, jb, d.U[q][2], jb, wb && g.bc[2] < 0);
-    }
-    {   // mu = 3 (x4)
-        const int st = g.L[1] * g.L[2];
-        const bool wf = x4 == g.L[3] - 1, wb = x4 == 0;
-        const int jf = x1h + g.Lh * (wf ? r - (g.L[3] - 1) * st : r + st);
-        const int jb = x1h + g.Lh * (wb ? r + (g.L[3] - 1) * st : r - st);
-        hop_dir<P, 3, SF, false>(acc, in, jf, d.U[p][3], i, wf && g.bc[3] < 0);
-        hop_dir<P, 3, SB, true>(acc, in, jb, d.U[q][3], jb, wb && g.bc[3] < 0);
+    constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma (backward: 1 - SF gamma)
+    if (HopPrefetch<P>::value) {
+        Raw<P> cur, nxt;
+        load_raw(cur, in, jn[0], d.U[p][0], ju[0]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k < 7) load_raw(nxt, in, jn[k + 1], d.U[((k + 1) & 1) ? q : p][(k + 1) >> 1], ju[k + 1]);
+            hop_term_d<P, SF>(k, acc, cur, flip[k]);
+            if (k < 7) cur = nxt;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            Raw<P> cur;
+            load_raw(cur, in, jn[k], d.U[(k & 1) ? q : p][k >> 1], ju[k]);
+            hop_term_d<P, SF>(k, acc, cur, flip[k]);
+        }
     }
 
     const real a = (real)(hp.a_sign * d.kappa);
@@ -226,10 +350,16 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     const int B = tuned_block(key, st, run, out != y && out != in, HopMaxThreads<P>::value);
     double sites = 0;
     for (auto& sd : b.sys) sites += sd.g.Vh;
-    ProfScope prof(P, sites * hop_bytes_per_site(P, MODE), st);
+    const double bps = hop_bytes_per_site(P, MODE);
+    ProfScope prof(P, sites * bps, st);
     run(B);
     count_launch();
     BPP_CHECK_LAUNCH();
+    if (thread_capturing()) {
+        for (int s = 0; s < b.nsys(); ++s) capture_hop_work(P, s, b.sys[s].g.Vh * bps);
+    } else {
+        add_hop_work(P, 1, sites * bps);
+    }
 }
 
 template <int P, bool DAG>

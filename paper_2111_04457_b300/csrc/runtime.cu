@@ -17,6 +17,36 @@ static std::atomic<int64_t> g_launches{0};
 static thread_local bool t_capturing = false;
 
 void set_capturing(bool on) { t_capturing = on; }
+bool thread_capturing() { return t_capturing; }
+
+static std::mutex g_work_mu;
+static int64_t g_work_n[3] = {0, 0, 0};
+static double g_work_bytes[3] = {0, 0, 0};
+static thread_local std::vector<double> t_cap_bytes;
+static thread_local int t_cap_prec = 0;
+
+void add_hop_work(int prec, int64_t launches, double bytes) {
+    std::lock_guard<std::mutex> lk(g_work_mu);
+    g_work_n[prec] += launches;
+    g_work_bytes[prec] += bytes;
+}
+void capture_hop_work(int prec, int sys, double bytes) {
+    if ((int)t_cap_bytes.size() <= sys) t_cap_bytes.resize(sys + 1, 0.0);
+    t_cap_bytes[sys] += bytes;
+    t_cap_prec = prec;
+}
+void capture_work_reset(int nsys) { t_cap_bytes.assign(nsys, 0.0); }
+const std::vector<double>& capture_work_bytes() { return t_cap_bytes; }
+int capture_work_prec() { return t_cap_prec; }
+
+int work_read(int prec, int64_t* n, double* bytes, int reset) {
+    if (prec < 0 || prec > 2) return BPP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_work_mu);
+    if (n) *n = g_work_n[prec];
+    if (bytes) *bytes = g_work_bytes[prec];
+    if (reset) { g_work_n[prec] = 0; g_work_bytes[prec] = 0; }
+    return 0;
+}
 
 void count_launch(int64_t n) {
     if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);

@@ -80,6 +80,7 @@ struct Plan {
     cudaGraphExec_t exec = nullptr;
     int graph_max_iter = -1;
     int body_kernels = 0;
+    std::vector<double> iter_bytes;      // hopping-kernel bytes of one iteration, per system
     size_t bytes = 0;
     uint64_t last_use = 0;
     ~Plan() {
@@ -245,6 +246,7 @@ static void build_graph(Plan& pl, int max_iter) {
         BPP_CUDA(cudaGraphAddNode(&node, pl.graph, nullptr, nullptr, 0, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         BPP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        capture_work_reset(pl.bP.nsys());
         set_capturing(true);
         try {
             BlasVecs v = inner_vecs(pl);
@@ -258,6 +260,7 @@ static void build_graph(Plan& pl, int max_iter) {
             throw;
         }
         set_capturing(false);
+        pl.iter_bytes = capture_work_bytes();
         cudaGraph_t captured;
         BPP_CUDA(cudaStreamEndCapture(cs, &captured));
         BPP_CUDA(cudaGraphInstantiate(&pl.exec, pl.graph, 0));
@@ -283,6 +286,9 @@ static void inner_solve(Plan& pl, const bpp_solve_opts& o, cudaStream_t st) {
         BPP_CUDA(cudaMemcpyAsync(&loops, pl.dloops.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         read_scalars(pl.dP, pl.hP, st);
         count_launch((int64_t)loops * pl.body_kernels);
+        double bytes = 0.0;
+        for (int s = 0; s < pl.bP.nsys() && s < (int)pl.iter_bytes.size(); ++s) bytes += pl.hP[s].iter * pl.iter_bytes[s];
+        add_hop_work(pl.prec, (int64_t)loops * 4, bytes);
         return;
     }
     // eager: host checks every check_every iterations; the hopping kernels and
@@ -352,71 +358,114 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
     }
 
-    // Schur-residual target per system: ||bhat - Mhat x|| <= target * ||b||
-    std::vector<double> target(n, tol);
+    // Outer loop.  r holds the even defect; after a "full" residual it is the
+    // even part of b - D x (equal to bhat - Mhat x_e, since x_o is
+    // reconstructed from x_e) and rr_o the odd part, so the full FP64 true
+    // residual is known.  A correction predicted to reach the target is
+    // followed directly by the full residual (3 hopping launches) instead of the
+    // Schur residual (2) plus a separate check (3).
+    std::vector<double> target(n, tol), rr_e(n, 0.0), rr_o(n, 0.0), pred(n, 0.0);
     std::vector<int> outer(n, 0), inner_it(n, 0), conv(n, 0), status(n, BPP_OK);
     std::vector<double> true_res(n, 0.0);
-    const int max_checks = 4;
-    for (int check = 0; check < max_checks; ++check) {
-        for (int it = 0; it < o.max_outer; ++it) {
-            // r = bhat - Mhat x (x = 0: r = bhat without a matrix application)
-            if (x_zero) {
-                BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
-                x_zero = false;
-            } else {
-                schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
-            }
-            outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
-            read_scalars(pl.d64, h64, st);
-            bool all = true;
-            for (int s = 0; s < n; ++s) {
-                if (!std::isfinite(h64[s].rr)) { status[s] = BPP_ERR_NONFINITE; h64[s].scale = 0.0; continue; }
-                const double rel = std::sqrt(h64[s].rr / std::max(bnorm2[s], 1e-300));
-                if (rel <= target[s] || bnorm2[s] == 0.0 || status[s] != BPP_OK) { h64[s].scale = 0.0; continue; }
-                all = false;
-            }
-            if (all) break;
-            write_scalars(pl.d64, h64, st);
-            // inner solve of Mhat e = r/||r||
-            for (int s = 0; s < n; ++s) {
-                KScal k{};
-                const double rn = std::sqrt(std::max(h64[s].rr, 0.0));
-                const double need = 0.5 * target[s] * std::sqrt(bnorm2[s]) / std::max(rn, 1e-300);
-                double itol = (bP.prec == P64 || o.inner_tol <= 0.0) ? need : std::max(o.inner_tol, need);
-                k.tol2 = itol * itol;
-                k.max_iter = o.max_inner;
-                hP[s] = k;
-                if (h64[s].scale > 0.0) outer[s] += 1;
-            }
-            write_scalars(pl.dP, hP, st);
-            outer_downcast(b64, bP, pl.r.p(), pl.w[0].p(), sc64, st);
-            inner_solve(pl, o, st);
-            for (int s = 0; s < n; ++s) inner_it[s] += h64[s].scale > 0.0 ? hP[s].iter : 0;
-            outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st);
-        }
-        // x_o = A_oo^-1 (b_o + kappa H_oe x_e)
+    bool have_full = false;
+    auto read_rr = [&](std::vector<double>& dst) {
+        read_scalars(pl.d64, h64, st);
+        for (int s = 0; s < n; ++s) dst[s] = h64[s].rr;
+    };
+    auto schur_residual = [&]() {
+        schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
+        outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+        read_rr(rr_e);
+        have_full = false;
+    };
+    auto full_residual = [&]() {
+        // x_o = A_oo^-1 (b_o + kappa H_oe x_e); De = A_ee x_e - kappa H_eo x_o; Do = A_oo x_o - kappa H_oe x_e
         hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), st);
-        // true residual with the full FP64 D: De = A_ee x_e - kappa H_eo x_o, Do = A_oo x_o - kappa H_oe x_e
         hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xo.p(), pl.r.p(), pl.xe.p(), st);
         outer_residual(b64, pl.be.p(), pl.r.p(), sc64, pl.rb, st);
-        read_scalars(pl.d64, h64, st);
-        std::vector<double> rr(n);
-        for (int s = 0; s < n; ++s) rr[s] = h64[s].rr;
+        read_rr(rr_e);
         hop(b64, 1, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xe.p(), pl.tmpo.p(), pl.xo.p(), st);
         outer_residual(b64, pl.bo.p(), pl.tmpo.p(), sc64, pl.rb, st);
-        read_scalars(pl.d64, h64, st);
-        bool again = false;
+        read_rr(rr_o);
+        have_full = true;
+        // outer_residual left the odd norm in the scalars; restore the even one
+        // for the downcast of the next correction
+        for (int s = 0; s < n; ++s) { h64[s].rr = rr_e[s]; h64[s].scale = std::sqrt(std::max(rr_e[s], 0.0)); }
+        write_scalars(pl.d64, h64, st);
+    };
+    if (x_zero) {
+        BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
+        outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+        read_rr(rr_e);
+    } else {
+        schur_residual();
+    }
+    const int max_passes = o.max_outer + 8;
+    for (int pass = 0; pass < max_passes; ++pass) {
+        bool need_check = false, any_active = false;
+        std::vector<int> active(n, 0);
         for (int s = 0; s < n; ++s) {
-            rr[s] += h64[s].rr;
-            true_res[s] = bnorm2[s] > 0.0 ? std::sqrt(rr[s] / bnorm2[s]) : 0.0;
-            if (!std::isfinite(true_res[s])) status[s] = BPP_ERR_NONFINITE;
-            conv[s] = status[s] == BPP_OK && true_res[s] <= tol;
-            if (!conv[s] && status[s] == BPP_OK) {
-                again = true;
-                target[s] = target[s] * 0.5 * tol / std::max(true_res[s], 1e-300);
+            if (status[s] != BPP_OK || conv[s]) continue;
+            const double rr = rr_e[s] + (have_full ? rr_o[s] : 0.0);
+            if (!std::isfinite(rr)) { status[s] = BPP_ERR_NONFINITE; continue; }
+            const double rel = bnorm2[s] > 0.0 ? std::sqrt(rr / bnorm2[s]) : 0.0;
+            if (bnorm2[s] == 0.0) { conv[s] = 1; true_res[s] = 0.0; continue; }
+            if (have_full) {
+                true_res[s] = rel;
+                if (rel <= tol) { conv[s] = 1; continue; }
+                if (rel <= target[s]) target[s] *= 0.5 * tol / rel;    // Schur target met but not the true one
+            } else if (rel <= target[s]) {
+                need_check = true;                                      // confirm with the full residual
+                continue;
             }
+            if (outer[s] >= o.max_outer) continue;
+            active[s] = 1;
+            any_active = true;
         }
-        if (!again) break;
+        if (need_check && !have_full) { full_residual(); continue; }
+        if (!any_active) break;
+        // inner solve of Mhat e = r/||r|| for the active systems
+        for (int s = 0; s < n; ++s) {
+            h64[s].rr = rr_e[s];
+            h64[s].scale = active[s] ? std::sqrt(std::max(rr_e[s], 0.0)) : 0.0;
+            KScal k{};
+            const double rn = std::sqrt(std::max(rr_e[s], 0.0));
+            const double need = 0.5 * target[s] * std::sqrt(bnorm2[s]) / std::max(rn, 1e-300);
+            // inner_tol <= 0: per-precision default (FP32 1e-6, FP16 2e-3)
+            const double dflt = bP.prec == P32 ? 1e-6 : 2e-3;
+            const double want = o.inner_tol > 0.0 ? o.inner_tol : dflt;
+            const double itol = bP.prec == P64 ? need : std::max(want, need);
+            k.tol2 = itol * itol;
+            k.max_iter = o.max_inner;
+            hP[s] = k;
+        }
+        write_scalars(pl.d64, h64, st);
+        write_scalars(pl.dP, hP, st);
+        outer_downcast(b64, bP, pl.r.p(), pl.w[0].p(), sc64, st);
+        inner_solve(pl, o, st);
+        outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st);
+        bool all_predicted = true;
+        for (int s = 0; s < n; ++s) {
+            if (!active[s]) continue;
+            outer[s] += 1;
+            inner_it[s] += hP[s].iter;
+            const double inner_rel = hP[s].bb > 0.0 ? std::sqrt(std::max(hP[s].rr, 0.0) / hP[s].bb) : 0.0;
+            pred[s] = std::sqrt(std::max(rr_e[s], 0.0)) * inner_rel;
+            if (!(pred[s] <= 0.5 * target[s] * std::sqrt(bnorm2[s]))) all_predicted = false;
+        }
+        if (all_predicted) full_residual();
+        else schur_residual();
+    }
+    if (!have_full) {
+        full_residual();
+        for (int s = 0; s < n; ++s) {
+            if (status[s] != BPP_OK || bnorm2[s] == 0.0) continue;
+            true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);
+            conv[s] = true_res[s] <= tol;
+        }
+    } else {
+        for (int s = 0; s < n; ++s)
+            if (status[s] == BPP_OK && bnorm2[s] > 0.0) true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);
     }
     for (int s = 0; s < n; ++s) eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st);
     BPP_CUDA(cudaStreamSynchronize(st));

@@ -220,3 +220,15 @@ def test_schur_equals_full_solve_residual():
     b = _rand_spinor(L, 2)
     x = oracle.solve(U, b, KAPPA, L, F=F, tol=1e-12)
     assert oracle.true_residual(U, b, x, KAPPA, L, F=F) < 1e-12
+
+
+def test_clover_field_sites_matches_full():
+    L = (4, 4, 4, 6)
+    U = synth.random_links(L)
+    F = oracle.clover_field(U, KAPPA, 1.0, L)
+    sites = np.array([0, 7, 100, oracle.volume(L) - 1])
+    assert np.array_equal(oracle.clover_field_sites(U, KAPPA, 1.0, L, sites), F[sites])
+    psi = _rand_spinor(L, 2)
+    full = oracle.apply_D(U, psi, KAPPA, L, F=F)
+    part = oracle.apply_D_sites_clover(U, psi, KAPPA, L, 1.0, sites)
+    assert np.abs(part - full[sites]).max() < 1e-13
