@@ -116,6 +116,27 @@ int bpp_clover_build(bpp_gauge g, double kappa, double csw, bpp_stream stream);
 int bpp_dslash(bpp_gauge U, const void* psi, void* out, double kappa, int parity, int prec,
                int nrhs, bpp_stream stream);
 
+/* bpp_dslash for the EVEN/ODD modes, for callers that cannot allocate device
+ * memory (a host application whose own memory manager owns the device and
+ * does not let libraries call cudaMalloc, or code that must not risk an
+ * allocation failing or stalling partway through).  No counterpart in the
+ * paper: it is the same hopping term as bpp_dslash, with the call's working
+ * storage (the system table and the two internal half fields) taken from one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until exit, instead of being allocated.  Arguments, layouts and results are
+ * those of bpp_dslash with parity BPP_EVEN or BPP_ODD (BPP_FULL is rejected).
+ * Needs 256-byte-rounded 64 system descriptors plus 2 * nrhs half fields of
+ * (Vh rounded up to 64) * {192, 96, 52} bytes for F64/F32/F16; larger requests
+ * return BPP_ERR_INVALID_ARG with the sizes in the message.  The current device
+ * must be the gauge field's device.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) and should come before
+ * any stream capture.  All calls share the one array: calls that can overlap
+ * on the GPU (different streams without ordering between them) race and give
+ * wrong results; calls on one stream are ordered and safe.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine. */
+int bpp_dslash_noalloc(bpp_gauge U, const void* psi, void* out, double kappa, int parity, int prec,
+                       int nrhs, bpp_stream stream);
+
 /* Clover term of Eq. (1) on one parity: out = (1 + F) in, or (1 + F)^{-1} in
  * when inverse != 0.  in/out: device, canonical half fields [nrhs][Vh][4][3]
  * of complex<prec>; parity BPP_EVEN or BPP_ODD.  Requires bpp_clover_build.

@@ -71,6 +71,7 @@ _SIGS = {
     "bpp_gauge_destroy": ([_p], _i),
     "bpp_clover_build": ([_p, _d, _d, _p], _i),
     "bpp_dslash": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
+    "bpp_dslash_noalloc": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
     "bpp_clover_apply": ([_p, _p, _p, _i, _i, _i, _i, _p], _i),
     "bpp_schur_apply": ([_p, _p, _p, _d, _d, _i, _i, _i, _p], _i),
     "bpp_dirac_apply": ([_p, _p, _p, _d, _d, _i, _i, _p], _i),
@@ -219,6 +220,22 @@ def dslash(g: Gauge, psi: torch.Tensor, kappa: float, parity: int, prec: int = F
     psi = psi.contiguous()
     out = torch.empty_like(psi)
     _check(_lib.bpp_dslash(g.handle, _ptr(psi), _ptr(out), float(kappa), parity, prec, n, _stream(stream)))
+    return out
+
+
+def dslash_noalloc(g: Gauge, psi: torch.Tensor, kappa: float, parity: int, prec: int = F64, out=None, stream=None):
+    """The EVEN/ODD hopping term of dslash() without any device allocation by
+    the library: for callers whose device memory is owned by another manager.
+    The library's working storage is a fixed 32 MiB device array (requests that
+    need more raise BppError); concurrent calls on unordered streams race."""
+    _cuda(psi, "psi")
+    if psi.dtype != _cdtype(prec):
+        raise ValueError(f"psi must be {_cdtype(prec)} for precision {prec}")
+    n = _nrhs(psi, 12 * g.lattice.Vh)
+    psi = psi.contiguous()
+    if out is None:
+        out = torch.empty_like(psi)
+    _check(_lib.bpp_dslash_noalloc(g.handle, _ptr(psi), _ptr(out), float(kappa), parity, prec, n, _stream(stream)))
     return out
 
 

@@ -29,6 +29,11 @@ static int fail(int code, const std::string& m) {
     return code;
 }
 
+namespace bpp {
+// Records an error for bpp_last_error from entry points defined in other files.
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace bpp
+
 template <class F>
 static int guard(const char* fn, F f) {
     try {

@@ -391,3 +391,40 @@ void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in,
 }
 
 }  // namespace bpp
+
+namespace bpp {
+
+// Hopping-kernel launch for the non-allocating entry point: fixed block size,
+// no autotuner lookup, no timing events, the system table already resident
+// on the device (dsys); all systems share one lattice (uniform map).
+void hop_fixed(int prec, const SysDesc* dsys, int nsys, int Vh, int parity, int mode, double a_sign, char* in,
+               char* out, char* y, cudaStream_t st) {
+    constexpr int B = 128;
+    HopParams hp;
+    hp.sys = dsys;
+    hp.parity = parity;
+    hp.in = in;
+    hp.out = out;
+    hp.y = y;
+    hp.a_sign = a_sign;
+    hp.done = nullptr;
+    hp.done_stride = 0;
+    hp.map.nsys = nsys;
+    hp.map.uniform = 1;
+    hp.map.tiles_per_sys = (Vh + B - 1) / B;
+    for (int s = 0; s <= MAXSYS; ++s) hp.map.tile_start[s] = 0;
+    const int nb = hp.map.tiles_per_sys * nsys;
+    if (prec == P64) {
+        if (mode == HOP_XPAY) k_hop<P64, false, HOP_XPAY><<<nb, B, 0, st>>>(hp);
+        else k_hop<P64, false, HOP_PLAIN><<<nb, B, 0, st>>>(hp);
+    } else if (prec == P32) {
+        if (mode == HOP_XPAY) k_hop<P32, false, HOP_XPAY><<<nb, B, 0, st>>>(hp);
+        else k_hop<P32, false, HOP_PLAIN><<<nb, B, 0, st>>>(hp);
+    } else {
+        if (mode == HOP_XPAY) k_hop<P16, false, HOP_XPAY><<<nb, B, 0, st>>>(hp);
+        else k_hop<P16, false, HOP_PLAIN><<<nb, B, 0, st>>>(hp);
+    }
+    count_launch();
+}
+
+}  // namespace bpp

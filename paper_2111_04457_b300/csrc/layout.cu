@@ -151,3 +151,31 @@ void int_to_half(const Batch& b, const char* in, void* canon, int canon_f64, cud
 }
 
 }  // namespace bpp
+
+namespace bpp {
+
+// Half-field conversions for the non-allocating entry point: the system
+// table (nsys systems of one lattice with Vh sites) is already on the device.
+void half_to_int_fixed(int prec, const SysDesc* dsys, int nsys, int Vh, const void* canon, int canon_f64, char* out,
+                       cudaStream_t st) {
+    const int B = 256;
+    dim3 grid((unsigned)((Vh + B - 1) / B), nsys);
+    BPP_PREC_DISPATCH(prec, {
+        if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(dsys, static_cast<const double2*>(canon), out);
+        else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(dsys, static_cast<const float2*>(canon), out);
+    });
+    count_launch();
+}
+
+void int_to_half_fixed(int prec, const SysDesc* dsys, int nsys, int Vh, const char* in, void* canon, int canon_f64,
+                       cudaStream_t st) {
+    const int B = 256;
+    dim3 grid((unsigned)((Vh + B - 1) / B), nsys);
+    BPP_PREC_DISPATCH(prec, {
+        if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(dsys, in, static_cast<double2*>(canon));
+        else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(dsys, in, static_cast<float2*>(canon));
+    });
+    count_launch();
+}
+
+}  // namespace bpp
