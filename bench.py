@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--inner-tol", type=float, default=None, help="inner relative tolerance")
     ap.add_argument("--eager", action="store_true", help="host-driven inner loop instead of CUDA graphs")
+    ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
+                    help="solve: the timed mixed-precision solve (default); dslash: the hopping kernel alone")
+    ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "f64df"], help="precision for --mode dslash")
     return ap.parse_args()
 
 
@@ -241,7 +244,7 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    for p in (0, 1, 2):
+    for p in (0, 1, 2, 3):
         bpp.work_read(p, reset=True)
     bpp.launch_count(reset=True)
     barrier(world)
@@ -257,7 +260,7 @@ def run_ours(args, rank, world):
     barrier(world)
     ms_local = e0.elapsed_time(e1)
     launches = bpp.launch_count()
-    work = {p: bpp.work_read(p, reset=True) for p in (0, 1, 2)}
+    work = {p: bpp.work_read(p, reset=True) for p in (0, 1, 2, 3)}
     clk = clocks.stop()
     ms = allreduce_max(ms_local, world, dev)
     hop_bytes = sum(v[1] for v in work.values())
@@ -269,12 +272,12 @@ def run_ours(args, rank, world):
     # solve of the same workload with the host-driven loop, every hopping launch
     # bracketed by CUDA events on its stream
     bpp.prof_enable(True)
-    for p in (0, 1, 2):
+    for p in (0, 1, 2, 3):
         bpp.prof_read(p, reset=True)
     bpp.solve(g, b, KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=False), x=x)
     torch.cuda.synchronize()
     bpp.prof_enable(False)
-    prof = {p: bpp.prof_read(p, reset=True) for p in (0, 1, 2)}
+    prof = {p: bpp.prof_read(p, reset=True) for p in (0, 1, 2, 3)}
     n_in, ms_in, by_in = prof[inner]
     n64, ms64, by64 = prof[0]
     peak_hbm, peak_kind = measured_peaks()
@@ -294,7 +297,13 @@ def run_ours(args, rank, world):
                 "kernel": "k_hop FP64 (outer defect correction)", "peak_kind": "derived: 148 SM x 2 DFMA/clk x 2 GHz",
                 "launches": n64, "avg_us": 1000 * ms64 / max(n64, 1), "share_ms": ms64,
                 "hbm_gbs": (by64 / (ms64 / 1000.0) / 1e9) if ms64 > 0 else None}
-    dominant = roof_f64 if ms64 > ms_in else roof_inner
+    nd, msd, byd = prof[3]
+    df_gbs = byd / (msd / 1000.0) / 1e9 if msd > 0 else None
+    roof_df = {"bound": "alu", "achieved": df_gbs, "peak": peak_hbm, "unit": "GB/s",
+               "frac": (df_gbs / peak_hbm) if df_gbs else None, "traffic": None,
+               "kernel": "k_hop double-float (outer defects, FP32 pipe)", "peak_kind": peak_kind,
+               "launches": nd, "avg_us": 1000 * msd / max(nd, 1), "share_ms": msd}
+    dominant = max([roof_f64, roof_inner, roof_df], key=lambda r: r["share_ms"])
 
     # e2e: host pinned b -> solve (library copies in and out) -> host x
     b_host = torch.from_numpy(b_np).pin_memory()
@@ -324,6 +333,16 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         fp64_ms = e0.elapsed_time(e1)
+    native_outer_ms = None
+    if not args.no_fp64:
+        on = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=not args.eager, outer_df64=False)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, on, x=x)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, on, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        native_outer_ms = e0.elapsed_time(e1)
     f32_ms = None
     if inner != bpp.F32:
         o32 = bpp.solve_opts(inner_prec=bpp.F32)
@@ -359,12 +378,13 @@ def run_ours(args, rank, world):
         "solve_ms": ms_step,
         "solve_ms_fp64": fp64_ms,
         "solve_ms_f32_inner": f32_ms,
+        "solve_ms_fp64_outer_defects": native_outer_ms,
         "speedup_vs_fp64": (fp64_ms / ms_step) if fp64_ms else None,
         "true_resid": true_res,
         "inner_tol": inner_tol,
         "graphs": not args.eager,
         "inner_iters": stats[-1]["inner_iters"], "outer_iters": stats[-1]["outer_iters"],
-        "hop_launches_per_step": {["f64", "f32", "f16"][p]: work[p][0] / args.steps for p in work},
+        "hop_launches_per_step": {["f64", "f32", "f16", "f64df"][p]: work[p][0] / args.steps for p in work},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": V * 12 * 16,
                 "d2h_bytes_per_step": V * 12 * 16, "ms_per_step": e2e_ms / args.steps},
@@ -372,10 +392,53 @@ def run_ours(args, rank, world):
         "roofline": dominant,
         "roofline_inner": roof_inner,
         "roofline_fp64": roof_f64,
+        "roofline_f64df": roof_df,
         "roofline_timing": "CUDA events around each hopping launch of one extra host-driven solve of the same workload",
         "cpu_baseline": cpu,
     }
     print(json.dumps(out), flush=True)
+
+
+def run_dslash(args, rank, world):
+    """The even-odd hopping kernel alone through bpp_dslash (EVEN output from an
+    ODD half field), CUDA events around each hopping launch."""
+    import torch
+
+    import paper_2111_04457_b300 as bpp
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else L_BENCH
+    prec = {"f64": bpp.F64, "f32": bpp.F32, "f16": bpp.F16, "f64df": bpp.F64DF}[args.prec]
+    g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
+    Vh = L[0] * L[1] * L[2] * L[3] // 2
+    dt = torch.complex128 if prec in (bpp.F64, bpp.F64DF) else torch.complex64
+    psi = torch.from_numpy(synth.gaussian_spinor(L, seed=2)[:Vh]).to(device=dev, dtype=dt)
+    for _ in range(args.warmup):
+        bpp.dslash(g, psi, KAPPA, bpp.EVEN, prec)
+    torch.cuda.synchronize()
+    bpp.prof_enable(True)
+    bpp.prof_read(prec, reset=True)
+    barrier(world)
+    for _ in range(args.steps):
+        bpp.dslash(g, psi, KAPPA, bpp.EVEN, prec)
+    torch.cuda.synchronize()
+    bpp.prof_enable(False)
+    n, ms, by = bpp.prof_read(prec, reset=True)
+    ms = allreduce_max(ms, world, dev)
+    by = allreduce_sum(by, world, dev)
+    if rank != 0:
+        return
+    peak, kind = measured_peaks()
+    gbs = by / (ms / 1000.0) / 1e9
+    print(json.dumps({"metric": "dslash GB/s (hopping kernel alone)", "value": gbs, "unit": "GB/s", "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / max(n, 1) * world,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+                      "data": "synthetic", "config": {"workload": f"even-odd Wilson hopping term {'x'.join(map(str, L))}",
+                                                      "lattice": list(L)},
+                      "frac_of_hbm": gbs / peak, "peak_kind": kind, "gsites_per_s": n * Vh / (ms / 1000.0) / 1e9}),
+          flush=True)
 
 
 def main():
@@ -383,6 +446,8 @@ def main():
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "dslash":
+        run_dslash(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -30,8 +30,8 @@
  *     sites of one parity in lexicographic order.  L1 must be even.
  *   - Canonical link layout: complex128 [4][V][3][3], row-major U_mu(x)[a][b].
  *   - The complex element type of a canonical field is complex128 for BPP_F64
- *     and complex64 for BPP_F32 and BPP_F16 (FP16 is a storage format: the
- *     library converts at the boundary and computes in FP32).
+ *     and BPP_F64DF and complex64 for BPP_F32 and BPP_F16 (FP16 is a storage
+ *     format: the library converts at the boundary and computes in FP32).
  *
  * Errors: every function returns an int status, 0 = BPP_OK, < 0 an error code
  * below.  No C++ exception crosses the ABI.  bpp_last_error() copies the
@@ -63,7 +63,11 @@ enum {
     BPP_ERR_TIMEOUT = -7        /* a bounded device-side wait ran out */
 };
 
-typedef enum { BPP_F64 = 0, BPP_F32 = 1, BPP_F16 = 2 } bpp_prec;
+/* BPP_F64DF: FP64 values (complex128 at the boundary) with double-float
+ * arithmetic inside (each real held as an FP32 hi + lo pair, ~48-bit
+ * significand), which runs on the FP32 pipe; accepted by bpp_dslash and
+ * bpp_schur_apply. */
+typedef enum { BPP_F64 = 0, BPP_F32 = 1, BPP_F16 = 2, BPP_F64DF = 3 } bpp_prec;
 typedef enum { BPP_EVEN = 0, BPP_ODD = 1, BPP_FULL = 2 } bpp_parity;
 typedef enum { BPP_BICGSTAB = 0, BPP_CGNR = 1 } bpp_solver;
 
@@ -177,6 +181,12 @@ typedef struct {
     int use_graph;    /* nonzero: run each inner solve as one CUDA graph launch whose
                          conditional while node repeats one Krylov iteration until every
                          system has converged (no host round trip per iteration) */
+    int outer_arith;  /* 0: every outer-loop operator application in FP64 arithmetic;
+                         1: the even-odd preparation and the intermediate defects
+                         bhat - Mhat x in double-float arithmetic (FP64 values held as
+                         FP32 hi + lo pairs, ~48-bit significands, on the FP32 pipe),
+                         while the solution, its accumulation, all norms and the final
+                         true residual stay FP64 */
 } bpp_solve_opts;
 
 /* Per right-hand side statistics of a solve. */
@@ -190,7 +200,8 @@ typedef struct {
 } bpp_solve_stats;
 
 /* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 0 (per precision),
- * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 1. */
+ * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 1,
+ * outer_arith 1. */
 void bpp_solve_opts_default(bpp_solve_opts* opts);
 
 /* Solves D x = b (or D^dag x = b) for nrhs right-hand sides sharing the gauge

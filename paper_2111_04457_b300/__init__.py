@@ -28,7 +28,7 @@ if not os.path.exists(_SO):
 
 _lib = ctypes.CDLL(_SO)
 
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, F64DF = 0, 1, 2, 3
 EVEN, ODD, FULL = 0, 1, 2
 BICGSTAB, CGNR = 0, 1
 _ERR = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
@@ -52,7 +52,8 @@ class _Lattice(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("use_x0", ctypes.c_int),
-                ("dagger", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("dagger", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("outer_arith", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -117,7 +118,7 @@ def _cuda(t: torch.Tensor, what):
 
 
 def _cdtype(prec):
-    return torch.complex128 if prec == F64 else torch.complex64
+    return torch.complex128 if prec in (F64, F64DF) else torch.complex64
 
 
 def version() -> int:
@@ -279,7 +280,10 @@ def dirac_apply(g: Gauge, x: torch.Tensor, kappa: float, csw: float = 0.0, dagge
 
 
 def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000, max_outer=50, dagger=False,
-               check_every=4, use_x0=False, use_graph=True) -> SolveOpts:
+               check_every=4, use_x0=False, use_graph=True, outer_df64=True) -> SolveOpts:
+    """Solver options (bpp_solve_opts).  outer_df64: intermediate defects of the
+    FP64 outer loop in double-float arithmetic (the final true residual, the
+    solution accumulation and the norms stay FP64)."""
     o = SolveOpts()
     _lib.bpp_solve_opts_default(ctypes.byref(o))
     o.solver = solver
@@ -292,6 +296,7 @@ def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000,
     o.check_every = check_every
     o.use_x0 = int(use_x0)
     o.use_graph = int(use_graph)
+    o.outer_arith = int(outer_df64)
     return o
 
 

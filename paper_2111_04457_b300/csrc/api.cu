@@ -57,9 +57,11 @@ static bool is_device_ptr(const void* p) {
 }
 
 static void check_gauge(const Gauge* G) { BPP_REQUIRE(G != nullptr, BPP_ERR_INVALID_ARG, "NULL gauge handle"); }
-static void check_prec(int prec) {
-    BPP_REQUIRE(prec == BPP_F64 || prec == BPP_F32 || prec == BPP_F16, BPP_ERR_INVALID_ARG, "unknown precision");
+static void check_prec(int prec, bool allow_df = false) {
+    BPP_REQUIRE(prec == BPP_F64 || prec == BPP_F32 || prec == BPP_F16 || (allow_df && prec == BPP_F64DF),
+                BPP_ERR_INVALID_ARG, "unknown precision");
 }
+static int canon_is_f64(int prec) { return prec == BPP_F64 || prec == BPP_F64DF; }
 static void check_clover(const Gauge& G, double kappa, double csw) {
     if (csw == 0.0) return;
     BPP_REQUIRE(G.has_clover, BPP_ERR_UNSUPPORTED, "clover term not built (call bpp_clover_build)");
@@ -106,7 +108,7 @@ int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream strea
             G->Vh = V / 2;
             G->stride = pad_stride(G->Vh);
             BPP_CUDA(cudaGetDevice(&G->device));
-            for (int p = 0; p < 3; ++p) BPP_CUDA(cudaMalloc(&G->links[p], 8 * link_alloc_bytes(p, G->stride)));
+            for (int p = 0; p < NPREC; ++p) BPP_CUDA(cudaMalloc(&G->links[p], 8 * link_alloc_bytes(p, G->stride)));
             const size_t bytes = (size_t)V * 4 * 9 * 16;
             if (is_device_ptr(U_lex)) {
                 links_to_internal(*G, U_lex, st);
@@ -117,7 +119,7 @@ int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream strea
             }
             BPP_CUDA(cudaStreamSynchronize(st));
         } catch (...) {
-            for (int p = 0; p < 3; ++p) if (G->links[p]) cudaFree(G->links[p]);
+            for (int p = 0; p < NPREC; ++p) if (G->links[p]) cudaFree(G->links[p]);
             delete G;
             throw;
         }
@@ -131,7 +133,7 @@ int bpp_gauge_destroy(bpp_gauge g) {
         if (!g) return BPP_OK;
         drop_plans(g);
         cudaDeviceSynchronize();
-        for (int p = 0; p < 3; ++p) {
+        for (int p = 0; p < NPREC; ++p) {
             if (g->links[p]) cudaFree(g->links[p]);
             if (g->clover[p]) cudaFree(g->clover[p]);
         }
@@ -153,14 +155,14 @@ int bpp_dslash(bpp_gauge U, const void* psi, void* out, double kappa, int parity
                bpp_stream stream) {
     return guard("bpp_dslash", [&]() -> int {
         check_gauge(U);
-        check_prec(prec);
+        check_prec(prec, true);
         BPP_REQUIRE(psi && out && psi != out, BPP_ERR_INVALID_ARG, "NULL or aliased field");
         BPP_REQUIRE(nrhs >= 1 && nrhs <= MAXSYS, BPP_ERR_INVALID_ARG, "nrhs must be 1..64");
         BPP_REQUIRE(parity == BPP_EVEN || parity == BPP_ODD || parity == BPP_FULL, BPP_ERR_INVALID_ARG, "bad parity");
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         Batch b;
         build_batch(b, *U, prec, kappa, false, nrhs, st);
-        const int f64 = prec == BPP_F64;
+        const int f64 = canon_is_f64(prec);
         DevBuf vin(b.vec_bytes, st), vout(b.vec_bytes, st);
         if (parity != BPP_FULL) {
             half_to_int(b, psi, f64, vin.as<char>(), st);
@@ -202,14 +204,14 @@ int bpp_schur_apply(bpp_gauge U, const void* in, void* out, double kappa, double
                     int nrhs, bpp_stream stream) {
     return guard("bpp_schur_apply", [&]() -> int {
         check_gauge(U);
-        check_prec(prec);
+        check_prec(prec, true);
         check_clover(*U, kappa, csw);
         BPP_REQUIRE(in && out && in != out, BPP_ERR_INVALID_ARG, "NULL or aliased field");
         BPP_REQUIRE(nrhs >= 1 && nrhs <= MAXSYS, BPP_ERR_INVALID_ARG, "nrhs must be 1..64");
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         Batch b;
         build_batch(b, *U, prec, kappa, csw != 0.0, nrhs, st);
-        const int f64 = prec == BPP_F64;
+        const int f64 = canon_is_f64(prec);
         DevBuf vin(b.vec_bytes, st), vout(b.vec_bytes, st), tmp(b.vec_bytes, st);
         half_to_int(b, in, f64, vin.as<char>(), st);
         schur(b, csw != 0.0, dagger ? 1 : 0, vin.as<char>(), vout.as<char>(), tmp.as<char>(), st);
@@ -251,6 +253,7 @@ void bpp_solve_opts_default(bpp_solve_opts* o) {
     o->dagger = 0;
     o->check_every = 4;
     o->use_graph = 1;
+    o->outer_arith = 1;
 }
 
 int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs,

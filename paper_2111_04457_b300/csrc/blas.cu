@@ -7,6 +7,7 @@
 namespace bpp {
 
 constexpr int BLAS_B = 256;
+constexpr int BLAS_SPT = 4;   // sites per thread
 
 __host__ __device__ __forceinline__ double2 c2(double r, double i) { return make_double2(r, i); }
 __device__ __forceinline__ double2 cmul2(double2 a, double2 b) { return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -121,112 +122,124 @@ __device__ __forceinline__ void check_done(KScal& k) {
     if (k.iter >= k.max_iter) { k.done = 1; k.status = 2; }
 }
 
+// The update and reduction terms of one site i of system d.
 template <int P, int OP>
-__global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
+__device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d, int i, double2 al, double2 om,
+                                          double2 be, double red[4]) {
     using real = typename PT<P>::real;
     using A = Access<P>;
+    cx<real> a[12], b[12], c[12];
+    if (OP == B_INIT_BICG) {
+        A::load_spinor(sys_view<P>(bp.v.b, d), i, a);
+        A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
+        A::store_spinor(sys_view<P>(bp.v.rhat, d), i, a);
+        A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
+        A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
+        red[0] += (double)norm12(a);
+    } else if (OP == B_ALPHA) {
+        real re, im;
+        A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.v, d), i, b);
+        dot12(a, b, re, im);
+        red[0] += re; red[1] += im;
+    } else if (OP == B_S) {
+        const cx<real> alr = mkc<real>((real)al.x, (real)al.y);
+        A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.v, d), i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { c[k] = a[k]; cfma(c[k], -alr, b[k]); }
+        A::store_spinor(sys_view<P>(bp.v.s, d), i, c);
+    } else if (OP == B_OMEGA) {
+        real re, im;
+        A::load_spinor(sys_view<P>(bp.v.t, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.s, d), i, b);
+        dot12(a, b, re, im);
+        red[0] += re; red[1] += im; red[2] += (double)norm12(a);
+    } else if (OP == B_XR) {
+        const cx<real> alr = mkc<real>((real)al.x, (real)al.y), omr = mkc<real>((real)om.x, (real)om.y);
+        // x += alpha p + omega s
+        A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+        A::load_spinor(sys_view<P>(bp.v.s, d), i, c);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { cfma(a[k], alr, b[k]); cfma(a[k], omr, c[k]); }
+        A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
+        // r = s - omega t
+        A::load_spinor(sys_view<P>(bp.v.t, d), i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) cfma(c[k], -omr, b[k]);
+        A::store_spinor(sys_view<P>(bp.v.r, d), i, c);
+        A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
+        real re, im;
+        dot12(a, c, re, im);
+        red[0] += norm12(c); red[1] += re; red[2] += im;
+    } else if (OP == B_P) {
+        const cx<real> ber = mkc<real>((real)be.x, (real)be.y), omr = mkc<real>((real)om.x, (real)om.y);
+        A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+        A::load_spinor(sys_view<P>(bp.v.v, d), i, c);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            cfma(b[k], -omr, c[k]);     // p - omega v
+            cfma(a[k], ber, b[k]);      // r + beta (...)
+        }
+        A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+    } else if (OP == B_CG_INIT) {
+        A::load_spinor(sys_view<P>(bp.v.b, d), i, a);
+        A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
+        A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
+        red[0] += (double)norm12(a);
+    } else if (OP == B_CG_PZ) {
+        A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
+        A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+        red[0] += (double)norm12(a);
+    } else if (OP == B_CG_ALPHA) {
+        A::load_spinor(sys_view<P>(bp.v.w, d), i, a);
+        red[0] += (double)norm12(a);
+    } else if (OP == B_CG_XR) {
+        const real alr = (real)al.x;
+        A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a[k] = a[k] + alr * b[k];
+        A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.w, d), i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a[k] = a[k] - alr * b[k];
+        A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
+        red[0] += (double)norm12(a);
+    } else if (OP == B_CG_BETA) {
+        A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
+        red[0] += (double)norm12(a);
+    } else if (OP == B_NORM2) {
+        A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+        red[0] += (double)norm12(a);
+    }
+}
+
+// Each block covers BLAS_SPT * BLAS_B sites of one system, so the last block
+// of a reduction sums few per-block partials.
+template <int P, int OP>
+__global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     int s, tile;
     map_block(bp.map, s, tile);
     const SysDesc& d = bp.sys[s];
     KScal* K = bp.sc + s;
     const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2) || !K->done;
-    const int i = tile * blockDim.x + threadIdx.x;
-    const bool in = active && i < d.g.Vh;
     // scalars used by the update (read before any finalize of this launch)
     const double2 al = K->alpha, om = K->omega, be = K->beta;
     double red[4] = {0.0, 0.0, 0.0, 0.0};
-    if (in) {
-        cx<real> a[12], b[12], c[12];
-        if (OP == B_INIT_BICG) {
-            A::load_spinor(sys_view<P>(bp.v.b, d), i, a);
-            A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
-            A::store_spinor(sys_view<P>(bp.v.rhat, d), i, a);
-            A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+    if (active) {
+        const int base = tile * (BLAS_SPT * BLAS_B) + threadIdx.x;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
-            A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
-            red[0] = (double)norm12(a);
-        } else if (OP == B_ALPHA) {
-            real re, im;
-            A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.v, d), i, b);
-            dot12(a, b, re, im);
-            red[0] = re; red[1] = im;
-        } else if (OP == B_S) {
-            const cx<real> alr = mkc<real>((real)al.x, (real)al.y);
-            A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.v, d), i, b);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) { c[k] = a[k]; cfma(c[k], -alr, b[k]); }
-            A::store_spinor(sys_view<P>(bp.v.s, d), i, c);
-        } else if (OP == B_OMEGA) {
-            real re, im;
-            A::load_spinor(sys_view<P>(bp.v.t, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.s, d), i, b);
-            dot12(a, b, re, im);
-            red[0] = re; red[1] = im; red[2] = (double)norm12(a);
-        } else if (OP == B_XR) {
-            const cx<real> alr = mkc<real>((real)al.x, (real)al.y), omr = mkc<real>((real)om.x, (real)om.y);
-            // x += alpha p + omega s
-            A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
-            A::load_spinor(sys_view<P>(bp.v.s, d), i, c);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) { cfma(a[k], alr, b[k]); cfma(a[k], omr, c[k]); }
-            A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
-            // r = s - omega t
-            A::load_spinor(sys_view<P>(bp.v.t, d), i, b);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) cfma(c[k], -omr, b[k]);
-            A::store_spinor(sys_view<P>(bp.v.r, d), i, c);
-            A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
-            real re, im;
-            dot12(a, c, re, im);
-            red[0] = norm12(c); red[1] = re; red[2] = im;
-        } else if (OP == B_P) {
-            const cx<real> ber = mkc<real>((real)be.x, (real)be.y), omr = mkc<real>((real)om.x, (real)om.y);
-            A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
-            A::load_spinor(sys_view<P>(bp.v.v, d), i, c);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                cfma(b[k], -omr, c[k]);     // p - omega v
-                cfma(a[k], ber, b[k]);      // r + beta (...)
-            }
-            A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
-        } else if (OP == B_CG_INIT) {
-            A::load_spinor(sys_view<P>(bp.v.b, d), i, a);
-            A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
-            A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
-            red[0] = (double)norm12(a);
-        } else if (OP == B_CG_PZ) {
-            A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
-            A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
-            red[0] = (double)norm12(a);
-        } else if (OP == B_CG_ALPHA) {
-            A::load_spinor(sys_view<P>(bp.v.w, d), i, a);
-            red[0] = (double)norm12(a);
-        } else if (OP == B_CG_XR) {
-            const real alr = (real)al.x;
-            A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.p, d), i, b);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) a[k] = a[k] + alr * b[k];
-            A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.r, d), i, a);
-            A::load_spinor(sys_view<P>(bp.v.w, d), i, b);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) a[k] = a[k] - alr * b[k];
-            A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
-            red[0] = (double)norm12(a);
-        } else if (OP == B_CG_BETA) {
-            A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
-            red[0] = (double)norm12(a);
-        } else if (OP == B_NORM2) {
-            A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
-            red[0] = (double)norm12(a);
+        for (int k = 0; k < BLAS_SPT; ++k) {
+            const int i = base + k * BLAS_B;
+            if (i < d.g.Vh) blas_site<P, OP>(bp, d, i, al, om, be, red);
         }
     }
     constexpr bool HAS_RED = OP != B_S && OP != B_P;
@@ -298,15 +311,18 @@ __global__ void __launch_bounds__(BLAS_B) k_cg_p(BlasParams bp) {
     map_block(bp.map, s, tile);
     const SysDesc& d = bp.sys[s];
     if (bp.sc[s].done) return;
-    const int i = tile * blockDim.x + threadIdx.x;
-    if (i >= d.g.Vh) return;
     const real be = (real)bp.sc[s].beta.x;
-    cx<real> a[12], b[12];
-    Access<P>::load_spinor(sys_view<P>(bp.v.z, d), i, a);
-    Access<P>::load_spinor(sys_view<P>(bp.v.p, d), i, b);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) a[k] = a[k] + be * b[k];
-    Access<P>::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+    for (int k = 0; k < BLAS_SPT; ++k) {
+        const int i = tile * (BLAS_SPT * BLAS_B) + k * BLAS_B + threadIdx.x;
+        if (i >= d.g.Vh) break;
+        cx<real> a[12], b[12];
+        Access<P>::load_spinor(sys_view<P>(bp.v.z, d), i, a);
+        Access<P>::load_spinor(sys_view<P>(bp.v.p, d), i, b);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) a[c] = a[c] + be * b[c];
+        Access<P>::store_spinor(sys_view<P>(bp.v.p, d), i, a);
+    }
 }
 
 template <int P>
@@ -314,7 +330,7 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
     BlasParams bp;
     bp.sys = bt.dev();
     int nb = 0;
-    bp.map = block_map(bt, BLAS_B, nb);
+    bp.map = block_map(bt, BLAS_B * BLAS_SPT, nb);
     rb.ensure(nb, bt.nsys(), st);
     bp.v = vv;
     bp.sc = sc;
@@ -344,6 +360,7 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
 }
 
 void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st) {
+    BPP_REQUIRE(bt.prec != P64S, BPP_ERR_UNSUPPORTED, "Krylov vector kernels do not run on split-FP64 vectors");
     if (bt.prec == P64) blas_t<P64>(bt, op, vv, sc, rb, st);
     else if (bt.prec == P32) blas_t<P32>(bt, op, vv, sc, rb, st);
     else blas_t<P16>(bt, op, vv, sc, rb, st);
@@ -356,6 +373,7 @@ struct OuterParams {
     BlockMap map;
     char* a;
     char* b;
+    char* c;           // optional third vector (split-FP64 outputs / inputs)
     KScal* sc;
     double* partials;
     unsigned* tickets;
@@ -422,6 +440,64 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_acc(OuterParams op) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) x[k] = x[k] + sc * mkc<double>((double)e[k].r, (double)e[k].i);
     Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, x);
+    if (op.c) {
+        cx<df64> xs[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) xs[k] = mkc(df64(x[k].r), df64(x[k].i));
+        Access<P64S>::store_spinor(sys_view<P64S>(op.c, d), i, xs);
+    }
+}
+
+// r = bhat - m in FP64 from split-FP64 bhat (op.a) and m (op.b, may be null),
+// written to op.c, with ||r||^2 per system.  Split vectors share the FP64
+// vectors' offsets and strides (both 192 B per site).
+__global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    double red[4] = {0, 0, 0, 0};
+    if (i < d.g.Vh) {
+        cx<df64> bh[12], m[12];
+        cx<double> r[12];
+        Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, bh);
+        if (op.b) Access<P64S>::load_spinor(sys_view<P64S>(op.b, d), i, m);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            r[k] = mkc(bh[k].r.to_double(), bh[k].i.to_double());
+            if (op.b) r[k] = r[k] - mkc(m[k].r.to_double(), m[k].i.to_double());
+        }
+        Access<P64>::store_spinor(sys_view<P64>(op.c, d), i, r);
+        red[0] = norm12(r);
+    }
+    BlasParams bp;
+    bp.map = op.map;
+    bp.partials = op.partials;
+    bp.tickets = op.tickets;
+    double tot[4];
+    if (!reduce_sys<4>(bp, s, red, tot)) return;
+    if (threadIdx.x == 0) {
+        op.sc[s].rr = tot[0];
+        op.sc[s].scale = sqrt(tot[0]);
+    }
+}
+
+void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = b64.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    rb.ensure(nb, b64.nsys(), st);
+    op.a = bhat_s;
+    op.b = m_s;
+    op.c = r64;
+    op.sc = sc;
+    op.partials = rb.partials.as<double>();
+    op.tickets = rb.tickets.as<unsigned>();
+    k_split_residual<<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
 }
 
 void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
@@ -433,6 +509,7 @@ void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& 
     rb.ensure(nb, b64.nsys(), st);
     op.a = bhat;
     op.b = r64;
+    op.c = nullptr;
     op.sc = sc;
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
@@ -449,6 +526,7 @@ void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo
     op.map = block_map(b64, BLAS_B, nb);
     op.a = const_cast<char*>(r64);
     op.b = lo;
+    op.c = nullptr;
     op.sc = const_cast<KScal*>(sc);
     if (bP.prec == P64) k_outer_down<P64><<<nb, BLAS_B, 0, st>>>(op);
     else if (bP.prec == P32) k_outer_down<P32><<<nb, BLAS_B, 0, st>>>(op);
@@ -457,7 +535,8 @@ void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo
     BPP_CHECK_LAUNCH();
 }
 
-void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* e, const KScal* sc, cudaStream_t st) {
+void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* e, const KScal* sc, cudaStream_t st,
+                      char* x_split) {
     OuterParams op;
     op.s64 = b64.dev();
     op.sP = bP.dev();
@@ -465,6 +544,7 @@ void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* 
     op.map = block_map(b64, BLAS_B, nb);
     op.a = x64;
     op.b = const_cast<char*>(e);
+    op.c = x_split;
     op.sc = const_cast<KScal*>(sc);
     if (bP.prec == P64) k_outer_acc<P64><<<nb, BLAS_B, 0, st>>>(op);
     else if (bP.prec == P32) k_outer_acc<P32><<<nb, BLAS_B, 0, st>>>(op);

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/bpp.h"
+#include "df64.h"
 
 namespace bpp {
 
@@ -53,7 +54,10 @@ struct Error : public std::runtime_error {
 #define BPP_CHECK_LAUNCH() BPP_CUDA(cudaGetLastError())
 
 // ----------------------------------------------------------------------------- precision
-enum Prec { P64 = BPP_F64, P32 = BPP_F32, P16 = BPP_F16 };
+// P64S is internal only: FP64 values stored as (hi, lo) FP32 pairs and used
+// with double-float arithmetic (df64.h); same bytes as FP64.
+enum Prec { P64 = BPP_F64, P32 = BPP_F32, P16 = BPP_F16, P64S = 3 };
+constexpr int NPREC = 4;
 
 template <int P> struct PT;
 template <> struct PT<P64> {
@@ -74,12 +78,18 @@ template <> struct PT<P16> {
     static constexpr int link_bytes = 36;
     static constexpr int clover_bytes = 144;
 };
+template <> struct PT<P64S> {
+    using real = df64;
+    static constexpr int spinor_bytes = 192;
+    static constexpr int link_bytes = 144;
+    static constexpr int clover_bytes = 576;
+};
 
 inline int spinor_bytes(int prec) {
-    return prec == P64 ? 192 : prec == P32 ? 96 : 52;
+    return (prec == P64 || prec == P64S) ? 192 : prec == P32 ? 96 : 52;
 }
 inline int link_bytes(int prec) {
-    return prec == P64 ? 144 : prec == P32 ? 72 : 36;
+    return (prec == P64 || prec == P64S) ? 144 : prec == P32 ? 72 : 36;
 }
 
 // ----------------------------------------------------------------------------- complex
@@ -132,7 +142,7 @@ struct CloverView {
 inline int64_t pad_stride(int64_t n) { return (n + 63) / 64 * 64; }
 
 inline size_t spinor_alloc_bytes(int prec, int64_t stride) {
-    if (prec == P64) return (size_t)stride * 192;
+    if (prec == P64 || prec == P64S) return (size_t)stride * 192;
     if (prec == P32) return (size_t)stride * 96;
     return (size_t)stride * 52;
 }
@@ -201,6 +211,32 @@ template <> struct Access<P32> {
         const float2* q = reinterpret_cast<const float2*>(p + 4 * u.stride);
         float2 v = __ldcs(q + i);
         m[8] = mkc(v.x, v.y);
+    }
+};
+
+// Split FP64: each complex component is one float4 (re.hi, re.lo, im.hi, im.lo).
+template <> struct Access<P64S> {
+    using real = df64;
+    static __device__ __forceinline__ void load_spinor(const SpinorView& f, int64_t i, cx<df64> s[12]) {
+        const float4* p = static_cast<const float4*>(f.data);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 v = __ldg(p + k * f.stride + i);
+            s[k] = mkc(df64(v.x, v.y), df64(v.z, v.w));
+        }
+    }
+    static __device__ __forceinline__ void store_spinor(const SpinorView& f, int64_t i, const cx<df64> s[12]) {
+        float4* p = static_cast<float4*>(f.data);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k * f.stride + i] = make_float4(s[k].r.hi, s[k].r.lo, s[k].i.hi, s[k].i.lo);
+    }
+    static __device__ __forceinline__ void load_link(const LinkView& u, int64_t i, cx<df64> m[9]) {
+        const float4* p = static_cast<const float4*>(u.data);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float4 v = __ldcs(p + k * u.stride + i);
+            m[k] = mkc(df64(v.x, v.y), df64(v.z, v.w));
+        }
     }
 };
 

@@ -59,9 +59,9 @@ struct CloverBuildParams {
     Geom g;
     LinkView U[2][4];     // FP64 links
     double kc;            // kappa * c_SW
-    void* out[3];         // per precision: A_e, A_o, Ainv_e, Ainv_o
+    void* out[NPREC];     // per storage format: A_e, A_o, Ainv_e, Ainv_o
     int64_t stride;
-    size_t field_bytes[3];
+    size_t field_bytes[NPREC];
     int* bad;             // set when a block is singular or non-finite
 };
 
@@ -81,6 +81,13 @@ __device__ void store_block(const CloverBuildParams& cp, int which, int parity, 
         for (int k = 0; k < 36; ++k) {
             const int h = blk * 36 + k;
             base[((h >> 3) * cp.stride + i) * 8 + (h & 7)] = __double2half(r[k]);
+        }
+    }
+    {
+        float4* p = reinterpret_cast<float4*>(static_cast<char*>(cp.out[P64S]) + f * cp.field_bytes[P64S]);
+        for (int j = 0; j < 18; ++j) {
+            const df64 a(r[2 * j]), b(r[2 * j + 1]);
+            p[(blk * 18 + j) * cp.stride + i] = make_float4(a.hi, a.lo, b.hi, b.lo);
         }
     }
 }
@@ -209,7 +216,7 @@ __global__ void k_clover_build(CloverBuildParams cp) {
 }
 
 void clover_build(Gauge& G, double kappa, double csw, cudaStream_t st) {
-    for (int p = 0; p < 3; ++p) {
+    for (int p = 0; p < NPREC; ++p) {
         if (!G.clover[p]) BPP_CUDA(cudaMalloc(&G.clover[p], 4 * clover_alloc_bytes(p, G.stride)));
     }
     CloverBuildParams cp;
@@ -218,7 +225,7 @@ void clover_build(Gauge& G, double kappa, double csw, cudaStream_t st) {
         for (int m = 0; m < 4; ++m) cp.U[p][m] = link_view(G, P64, p, m);
     cp.kc = kappa * csw;
     cp.stride = G.stride;
-    for (int p = 0; p < 3; ++p) {
+    for (int p = 0; p < NPREC; ++p) {
         cp.out[p] = G.clover[p];
         cp.field_bytes[p] = clover_alloc_bytes(p, G.stride);
     }
@@ -261,7 +268,8 @@ void clover_apply(const Batch& b, int parity, int inverse, char* in, char* out, 
     dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
     if (b.prec == P64) k_clover_apply<P64><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
     else if (b.prec == P32) k_clover_apply<P32><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
-    else k_clover_apply<P16><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
+    else if (b.prec == P16) k_clover_apply<P16><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
+    else k_clover_apply<P64S><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
     count_launch();
     BPP_CHECK_LAUNCH();
 }

@@ -49,6 +49,18 @@ template <> struct CloverAccess<P16> {
     }
 };
 
+template <> struct CloverAccess<P64S> {
+    static __device__ __forceinline__ void load_block(const CloverView& c, int64_t i, int blk, df64 r[36]) {
+        const float4* p = static_cast<const float4*>(c.data);
+#pragma unroll
+        for (int j = 0; j < 18; ++j) {
+            float4 v = __ldg(p + (blk * 18 + j) * c.stride + i);
+            r[2 * j] = df64(v.x, v.y);
+            r[2 * j + 1] = df64(v.z, v.w);
+        }
+    }
+};
+
 // out = A in for one packed 6x6 Hermitian block r[36].
 template <class real>
 __device__ __forceinline__ void herm6_apply(const real r[36], const cx<real> in[6], cx<real> out[6]) {

@@ -1,0 +1,74 @@
+// Double-float ("df64") arithmetic: a real number as an unevaluated sum
+// hi + lo of two FP32 values (|lo| <= ulp(hi)/2), about 48 significant bits.
+// B300's FP64 pipe runs at ~1.1 TFLOP/s while its FP32 pipe runs at ~70, so
+// operator applications that need close-to-FP64 accuracy but not FP64
+// exactness (the intermediate defects of the FP64 outer loop) run faster in
+// this form on the FP32 pipe.
+//
+// Building blocks are the error-free transformations of Knuth (TwoSum) and
+// Dekker (FastTwoSum), with the product error taken from a fused multiply-add
+// (TwoProd).  Addition is the cheaper variant that adds the two low parts into
+// the error term (relative error ~2^-44 of the larger operand), which is ample
+// for defects down to 1e-12 relative.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bpp {
+
+struct df64 {
+    float hi, lo;
+    __host__ __device__ df64() {}
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ df64(int v) : hi((float)v), lo(0.f) {}
+    __device__ explicit df64(double v) {
+        hi = __double2float_rn(v);
+        lo = __double2float_rn(v - (double)hi);
+    }
+    __device__ double to_double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df64 quick_two_sum(float a, float b) {
+    const float s = a + b;
+    return df64(s, b - (s - a));
+}
+
+__device__ __forceinline__ df64 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return df64(s, (a - (s - bb)) + (b - bb));
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+    const df64 s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+
+// Exact-match overloads so that unqualified fma() inside this namespace keeps
+// resolving to the hardware FMA for float and double arguments.
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return ::fmaf(a, b, c); }
+
+// a * b + c
+__device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const df64 s = two_sum(p, c.hi);
+    return quick_two_sum(s.hi, s.lo + (e + c.lo));
+}
+
+}  // namespace bpp

@@ -93,6 +93,7 @@ template <int P> struct Raw;
 template <> struct Raw<P64> { double2 s[12]; double2 u[9]; };
 template <> struct Raw<P32> { float4 s[6]; float4 u[4]; float2 u8; };
 template <> struct Raw<P16> { uint4 s[3]; float sc; uint4 u[2]; unsigned u8; };
+template <> struct Raw<P64S> { float4 s[12]; float4 u[9]; };
 
 __device__ __forceinline__ void load_raw(Raw<P64>& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
     const double2* p = static_cast<const double2*>(in.data);
@@ -120,6 +121,21 @@ __device__ __forceinline__ void load_raw(Raw<P16>& r, const SpinorView& in, int6
 #pragma unroll
     for (int k = 0; k < 2; ++k) r.u[k] = __ldcs(q + k * U.stride + ju);
     r.u8 = __ldcs(reinterpret_cast<const unsigned*>(q + 2 * U.stride) + ju);
+}
+
+__device__ __forceinline__ void load_raw(Raw<P64S>& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
+    const float4* p = static_cast<const float4*>(in.data);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.s[k] = __ldg(p + k * in.stride + j);
+    const float4* q = static_cast<const float4*>(U.data);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r.u[k] = __ldcs(q + k * U.stride + ju);
+}
+__device__ __forceinline__ void decode(const Raw<P64S>& r, cx<df64> psi[12], cx<df64> u[9]) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) psi[k] = mkc(df64(r.s[k].x, r.s[k].y), df64(r.s[k].z, r.s[k].w));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = mkc(df64(r.u[k].x, r.u[k].y), df64(r.u[k].z, r.u[k].w));
 }
 
 __device__ __forceinline__ void decode(const Raw<P64>& r, cx<double> psi[12], cx<double> u[9]) {
@@ -204,10 +220,12 @@ __device__ __forceinline__ void hop_term_d(int d, cx<typename PT<P>::real> acc[1
 #endif
 template <int P> struct HopPrefetch { static constexpr bool value = BPP_HOP_PREFETCH != 0; };
 template <> struct HopPrefetch<P64> { static constexpr bool value = false; };
+template <> struct HopPrefetch<P64S> { static constexpr bool value = false; };
 
 // FP64 needs more registers per thread than a 512-thread block allows.
 template <int P> struct HopMaxThreads { static constexpr int value = 512; };
 template <> struct HopMaxThreads<P64> { static constexpr int value = 256; };
+template <> struct HopMaxThreads<P64S> { static constexpr int value = 256; };
 template <> struct HopMaxThreads<P16> { static constexpr int value = BPP_HOP16_MAXT; };
 
 template <int P, bool DAG, int MODE>
@@ -319,7 +337,7 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value) k_hop(HopParams hp) {
 
 double hop_bytes_per_site(int prec, int mode) {
     const double S = spinor_bytes(prec), L = link_bytes(prec);
-    const double C = prec == P64 ? 576 : prec == P32 ? 288 : 144;
+    const double C = (prec == P64 || prec == P64S) ? 576 : prec == P32 ? 288 : 144;
     double b = 8 * L + 2 * S;
     if (mode == HOP_XPAY) b += S;
     if (mode == HOP_CLOV_XPAY) b += S + C;
@@ -384,6 +402,9 @@ void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in,
     } else if (b.prec == P32) {
         dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
             : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
+    } else if (b.prec == P64S) {
+        dag ? launch_mode<P64S, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
+            : launch_mode<P64S, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
     } else {
         dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
             : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);

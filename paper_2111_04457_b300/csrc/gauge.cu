@@ -37,6 +37,16 @@ template <> struct LinkStore<P16> {
     }
 };
 
+template <> struct LinkStore<P64S> {
+    static __device__ void store(void* base, int64_t stride, int64_t i, const double2 m[9]) {
+        float4* p = static_cast<float4*>(base);
+        for (int k = 0; k < 9; ++k) {
+            const df64 re(m[k].x), im(m[k].y);
+            p[k * stride + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+};
+
 // One thread per (half-lattice site i, parity p, direction mu).
 template <int P>
 __global__ void k_links_in(Geom g, const double2* __restrict__ U, void* out, int64_t stride, size_t field_bytes) {
@@ -61,7 +71,8 @@ void links_to_internal(Gauge& G, const void* U_dev, cudaStream_t s) {
     k_links_in<P64><<<grid, B, 0, s>>>(G.g, static_cast<const double2*>(U_dev), G.links[P64], G.stride, link_alloc_bytes(P64, G.stride));
     k_links_in<P32><<<grid, B, 0, s>>>(G.g, static_cast<const double2*>(U_dev), G.links[P32], G.stride, link_alloc_bytes(P32, G.stride));
     k_links_in<P16><<<grid, B, 0, s>>>(G.g, static_cast<const double2*>(U_dev), G.links[P16], G.stride, link_alloc_bytes(P16, G.stride));
-    count_launch(3);
+    k_links_in<P64S><<<grid, B, 0, s>>>(G.g, static_cast<const double2*>(U_dev), G.links[P64S], G.stride, link_alloc_bytes(P64S, G.stride));
+    count_launch(4);
     BPP_CHECK_LAUNCH();
 }
 

@@ -9,10 +9,10 @@ struct bpp_gauge_s {
     bpp::Geom g;
     int64_t V = 0, Vh = 0, stride = 0;
     int device = 0;
-    void* links[3] = {nullptr, nullptr, nullptr};   // per precision: 8 link fields [parity][mu]
+    void* links[bpp::NPREC] = {};    // per storage format: 8 link fields [parity][mu]
     bool has_clover = false;
     double clov_kappa = 0.0, clov_csw = 0.0;
-    void* clover[3] = {nullptr, nullptr, nullptr};  // per precision: A_e, A_o, Ainv_e, Ainv_o
+    void* clover[bpp::NPREC] = {};   // per storage format: A_e, A_o, Ainv_e, Ainv_o
 };
 
 namespace bpp {
@@ -20,7 +20,7 @@ namespace bpp {
 using Gauge = bpp_gauge_s;
 
 inline size_t clover_alloc_bytes(int prec, int64_t stride) {
-    return (size_t)stride * (prec == P64 ? 576 : prec == P32 ? 288 : 144);
+    return (size_t)stride * ((prec == P64 || prec == P64S) ? 576 : prec == P32 ? 288 : 144);
 }
 
 inline LinkView link_view(const Gauge& G, int prec, int parity, int mu) {

@@ -21,6 +21,12 @@ template <> __device__ __forceinline__ double2 to_canon<double2, double>(cx<doub
 template <> __device__ __forceinline__ double2 to_canon<double2, float>(cx<float> v) { return make_double2(v.r, v.i); }
 template <> __device__ __forceinline__ float2 to_canon<float2, double>(cx<double> v) { return make_float2((float)v.r, (float)v.i); }
 template <> __device__ __forceinline__ float2 to_canon<float2, float>(cx<float> v) { return make_float2(v.r, v.i); }
+template <> __device__ __forceinline__ double2 to_canon<double2, df64>(cx<df64> v) {
+    return make_double2(v.r.to_double(), v.i.to_double());
+}
+template <> __device__ __forceinline__ float2 to_canon<float2, df64>(cx<df64> v) {
+    return make_float2((float)v.r.to_double(), (float)v.i.to_double());
+}
 
 // Thread per (half-lattice site, parity) of system sys0 + blockIdx.y.
 template <int P, class TC>
@@ -97,7 +103,8 @@ __global__ void k_int_to_half(const SysDesc* sys, const char* in, TC* canon) {
     do {                                                              \
         if ((prec) == P64) { constexpr int PP = P64; __VA_ARGS__; }        \
         else if ((prec) == P32) { constexpr int PP = P32; __VA_ARGS__; }   \
-        else { constexpr int PP = P16; __VA_ARGS__; }                      \
+        else if ((prec) == P16) { constexpr int PP = P16; __VA_ARGS__; }   \
+        else { constexpr int PP = P64S; __VA_ARGS__; }                     \
     } while (0)
 
 void full_to_eo(const Batch& b, int sys0, int nsys, const void* canon, int canon_f64, int64_t cstride,

@@ -20,8 +20,8 @@ void set_capturing(bool on) { t_capturing = on; }
 bool thread_capturing() { return t_capturing; }
 
 static std::mutex g_work_mu;
-static int64_t g_work_n[3] = {0, 0, 0};
-static double g_work_bytes[3] = {0, 0, 0};
+static int64_t g_work_n[NPREC] = {};
+static double g_work_bytes[NPREC] = {};
 static thread_local std::vector<double> t_cap_bytes;
 static thread_local int t_cap_prec = 0;
 
@@ -40,7 +40,7 @@ const std::vector<double>& capture_work_bytes() { return t_cap_bytes; }
 int capture_work_prec() { return t_cap_prec; }
 
 int work_read(int prec, int64_t* n, double* bytes, int reset) {
-    if (prec < 0 || prec > 2) return BPP_ERR_INVALID_ARG;
+    if (prec < 0 || prec >= NPREC) return BPP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_work_mu);
     if (n) *n = g_work_n[prec];
     if (bytes) *bytes = g_work_bytes[prec];
@@ -101,9 +101,9 @@ struct ProfRec {
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfRec> g_prof;
-static int64_t g_prof_n[3] = {0, 0, 0};
-static double g_prof_ms[3] = {0, 0, 0};
-static double g_prof_bytes[3] = {0, 0, 0};
+static int64_t g_prof_n[NPREC] = {};
+static double g_prof_ms[NPREC] = {};
+static double g_prof_bytes[NPREC] = {};
 
 ProfScope::ProfScope(int p, double b, cudaStream_t st) : prec(p), bytes(b), s(st), on(false) {
     {
@@ -147,7 +147,7 @@ int prof_enable(int on) {
 int prof_read(int prec, int64_t* n, double* ms, double* bytes, int reset) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof_drain_locked();
-    if (prec < 0 || prec > 2) return BPP_ERR_INVALID_ARG;
+    if (prec < 0 || prec >= NPREC) return BPP_ERR_INVALID_ARG;
     if (n) *n = g_prof_n[prec];
     if (ms) *ms = g_prof_ms[prec];
     if (bytes) *bytes = g_prof_bytes[prec];

@@ -69,8 +69,10 @@ struct Plan {
     std::vector<double> kappa;
     bool clover = false;
     int prec = P32, solver = BPP_BICGSTAB;
-    Batch b64, bP;
+    bool split = false;                  // double-float defects (split-FP64 vectors)
+    Batch b64, bP, b64s;
     Vec be, bo, bhat, xe, xo, r, tmpo;
+    Vec be_s, bo_s, bhat_s, xe_s, m_s, tmpo_s;
     Vec w[9];
     RedBuf rb;
     DevBuf d64, dP, dloops;
@@ -101,10 +103,11 @@ static void alloc_vec(Plan& pl, Vec& v, const Batch& b) {
 }
 
 static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<double>& kappa, bool clover, int prec,
-                      int solver, cudaStream_t st) {
+                      int solver, bool split, cudaStream_t st) {
     ++g_plan_clock;
     for (auto& p : g_plans)
-        if (p->G == G && p->kappa == kappa && p->clover == clover && p->prec == prec && p->solver == solver) {
+        if (p->G == G && p->kappa == kappa && p->clover == clover && p->prec == prec && p->solver == solver &&
+            p->split == split) {
             p->last_use = g_plan_clock;
             return *p;
         }
@@ -114,14 +117,17 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     pl->clover = clover;
     pl->prec = prec;
     pl->solver = solver;
+    pl->split = split;
     pl->b64.prec = P64;
     pl->bP.prec = prec;
+    pl->b64s.prec = P64S;
     for (size_t s = 0; s < G.size(); ++s) {
         batch_add(pl->b64, *G[s], kappa[s], clover);
         batch_add(pl->bP, *G[s], kappa[s], clover);
+        batch_add(pl->b64s, *G[s], kappa[s], clover);
     }
     // evict least recently used plans beyond the count or byte budget
-    const size_t need = 7 * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes;
+    const size_t need = (split ? 13 : 7) * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes;
     for (;;) {
         size_t total = need;
         for (auto& p : g_plans) total += p->bytes;
@@ -132,13 +138,13 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
         BPP_CUDA(cudaDeviceSynchronize());
         g_plans.erase(g_plans.begin() + lru);
     }
-    pl->b64.dsys.persistent = true;
-    pl->bP.dsys.persistent = true;
-    pl->b64.dsys.alloc_persistent(pl->b64.sys.size() * sizeof(SysDesc));
-    pl->bP.dsys.alloc_persistent(pl->bP.sys.size() * sizeof(SysDesc));
-    BPP_CUDA(cudaMemcpy(pl->b64.dsys.p, pl->b64.sys.data(), pl->b64.sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
-    BPP_CUDA(cudaMemcpy(pl->bP.dsys.p, pl->bP.sys.data(), pl->bP.sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    for (Batch* b : {&pl->b64, &pl->bP, &pl->b64s}) {
+        b->dsys.alloc_persistent(b->sys.size() * sizeof(SysDesc));
+        BPP_CUDA(cudaMemcpy(b->dsys.p, b->sys.data(), b->sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    }
     for (Vec* v : {&pl->be, &pl->bo, &pl->bhat, &pl->xe, &pl->xo, &pl->r, &pl->tmpo}) alloc_vec(*pl, *v, pl->b64);
+    if (split)
+        for (Vec* v : {&pl->be_s, &pl->bo_s, &pl->bhat_s, &pl->xe_s, &pl->m_s, &pl->tmpo_s}) alloc_vec(*pl, *v, pl->b64s);
     for (auto& v : pl->w) alloc_vec(*pl, v, pl->bP);
     const int n = (int)G.size();
     pl->rb.persistent = true;
@@ -316,7 +322,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     BPP_REQUIRE(o.max_inner > 0 && o.max_outer > 0 && o.check_every > 0, BPP_ERR_INVALID_ARG, "iteration caps must be positive");
 
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, st);
+    const bool split = o.outer_arith != 0;
+    Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, split, st);
     const Batch& b64 = pl.b64;
     const Batch& bP = pl.bP;
     KScal* sc64 = pl.d64.as<KScal>();
@@ -324,15 +331,26 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     std::vector<KScal>& hP = pl.hP;
     pl.rb.ensure(1, n, st);   // tickets
 
-    // b -> even/odd FP64 (gamma5 b for the adjoint solve)
-    for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, b_canon[s], 1, 0, pl.be.p(), pl.bo.p(), o.dagger ? 1 : 0, st);
+    // b -> even/odd FP64 (gamma5 b for the adjoint solve), and split FP64
+    const Batch& b64s = pl.b64s;
+    for (int s = 0; s < n; ++s) {
+        full_to_eo(b64, s, 1, b_canon[s], 1, 0, pl.be.p(), pl.bo.p(), o.dagger ? 1 : 0, st);
+        if (split) full_to_eo(b64s, s, 1, b_canon[s], 1, 0, pl.be_s.p(), pl.bo_s.p(), o.dagger ? 1 : 0, st);
+    }
     const int dag = 0;
-    // bhat = b_e + kappa H_eo A_oo^-1 b_o
-    if (clover) {
-        clover_apply(b64, 1, 1, pl.bo.p(), pl.tmpo.p(), st);
-        hop(b64, 0, dag, HOP_XPAY, +1.0, pl.tmpo.p(), pl.bhat.p(), pl.be.p(), st);
-    } else {
-        hop(b64, 0, dag, HOP_XPAY, +1.0, pl.bo.p(), pl.bhat.p(), pl.be.p(), st);
+    // bhat = b_e + kappa H_eo A_oo^-1 b_o (double-float when split)
+    {
+        const Batch& bb = split ? b64s : b64;
+        char* be_ = split ? pl.be_s.p() : pl.be.p();
+        char* bo_ = split ? pl.bo_s.p() : pl.bo.p();
+        char* tmp_ = split ? pl.tmpo_s.p() : pl.tmpo.p();
+        char* bh_ = split ? pl.bhat_s.p() : pl.bhat.p();
+        if (clover) {
+            clover_apply(bb, 1, 1, bo_, tmp_, st);
+            hop(bb, 0, dag, HOP_XPAY, +1.0, tmp_, bh_, be_, st);
+        } else {
+            hop(bb, 0, dag, HOP_XPAY, +1.0, bo_, bh_, be_, st);
+        }
     }
     // norms: ||b||^2 = ||b_e||^2 + ||b_o||^2
     std::vector<double> bnorm2(n);
@@ -353,9 +371,13 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     // initial guess
     bool x_zero = !o.use_x0;
     if (o.use_x0) {
-        for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
+        for (int s = 0; s < n; ++s) {
+            full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
+            if (split) full_to_eo(b64s, s, 1, x_canon[s], 1, 0, pl.xe_s.p(), pl.tmpo_s.p(), o.dagger ? 1 : 0, st);
+        }
     } else {
         BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
+        if (split) BPP_CUDA(cudaMemsetAsync(pl.xe_s.p(), 0, b64s.vec_bytes, st));
     }
 
     // Outer loop.  r holds the even defect; after a "full" residual it is the
@@ -373,8 +395,13 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         for (int s = 0; s < n; ++s) dst[s] = h64[s].rr;
     };
     auto schur_residual = [&]() {
-        schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
-        outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+        if (split) {
+            schur(b64s, clover, dag, pl.xe_s.p(), pl.m_s.p(), pl.tmpo_s.p(), st);
+            split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r.p(), sc64, pl.rb, st);
+        } else {
+            schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
+            outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+        }
         read_rr(rr_e);
         have_full = false;
     };
@@ -394,8 +421,12 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         write_scalars(pl.d64, h64, st);
     };
     if (x_zero) {
-        BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
-        outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+        if (split) {
+            split_residual(b64, pl.bhat_s.p(), nullptr, pl.r.p(), sc64, pl.rb, st);
+        } else {
+            BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
+            outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
+        }
         read_rr(rr_e);
     } else {
         schur_residual();
@@ -443,7 +474,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         write_scalars(pl.dP, hP, st);
         outer_downcast(b64, bP, pl.r.p(), pl.w[0].p(), sc64, st);
         inner_solve(pl, o, st);
-        outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st);
+        outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st, split ? pl.xe_s.p() : nullptr);
         bool all_predicted = true;
         for (int s = 0; s < n; ++s) {
             if (!active[s]) continue;

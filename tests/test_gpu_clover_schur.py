@@ -112,3 +112,16 @@ def test_clover_abelian_flux_spectrum():
     expect = np.sort(np.repeat([1 - KAPPA * CSW * np.sin(theta), 1 + KAPPA * CSW * np.sin(theta)], 6))
     for s in range(Vh):
         assert np.abs(np.sort(np.linalg.eigvalsh(A[s])) - expect).max() < 1e-14
+
+
+@pytest.mark.parametrize("csw", [0.0, CSW])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_schur_f64df(setup, csw, dagger):
+    """Schur operator in double-float arithmetic (the outer loop's defects): bar 1e-12."""
+    bpp = lib()
+    L, g, U, F = setup
+    S = oracle.Schur(U, KAPPA, L, BC, F if csw else None)
+    x = synth.gaussian_spinor(L, seed=4)[S.even]
+    ref = S.apply(x, dagger=dagger)
+    out = to_np(bpp.schur_apply(g, to_dev(x), KAPPA, csw, dagger, bpp.F64DF))
+    assert rel_err(out, ref) <= 1e-12

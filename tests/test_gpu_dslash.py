@@ -97,3 +97,19 @@ def test_dslash_free_field_plane_wave():
     out = to_np(bpp.dslash(g, to_dev(psi), KAPPA, bpp.FULL, bpp.F64))
     expect = phase[:, None, None] * (oracle.free_field_Dp(p, KAPPA) @ u)[None]
     assert np.abs(out - expect).max() < 1e-13 * np.abs(expect).max()
+
+
+@pytest.mark.parametrize("L", [(6, 6, 6, 10), (8, 8, 8, 8), (2, 4, 2, 6)])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_dslash_f64df(L, parity):
+    """FP64 values with double-float arithmetic (~48-bit significands): bar 1e-12."""
+    bpp = lib()
+    g, U = gauge(L)
+    Vh = oracle.volume(L) // 2
+    psi = synth.gaussian_spinor(L, seed=2)[:Vh]
+    ref = oracle.hop_eo(U, psi, KAPPA, L, parity, BC)
+    out = to_np(bpp.dslash(g, to_dev(psi), KAPPA, parity, bpp.F64DF))
+    err = rel_err(out, ref)
+    print(f"double-float dslash norm-relative error {err:.2e}")
+    assert err <= 1e-12
+    assert max_err(out, ref) <= 1e-12

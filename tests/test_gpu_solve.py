@@ -102,3 +102,20 @@ def test_solve_nonfinite_input(lat):
     bb[3, 1, 2] = np.nan
     with pytest.raises(bpp.BppError):
         bpp.solve(g, to_dev(bb), KAPPA, 0.0, TOL)
+
+
+@pytest.mark.parametrize("inner", [0, 1, 2])
+@pytest.mark.parametrize("outer_df64", [False, True])
+@pytest.mark.parametrize("csw", [0.0, 1.0])
+def test_solve_outer_arithmetic(inner, outer_df64, csw):
+    """Both outer-loop arithmetics reach the FP64 true residual (checked by the oracle)."""
+    bpp = lib()
+    L = (4, 4, 6, 8)
+    g, U = gauge(L)
+    F = None
+    if csw:
+        g.clover_build(KAPPA, csw)
+        F = oracle.clover_field(U, KAPPA, csw, L)
+    b = synth.gaussian_spinor(L, seed=2)
+    x, st = bpp.solve(g, to_dev(b), KAPPA, csw, TOL, bpp.solve_opts(inner_prec=inner, outer_df64=outer_df64))
+    assert oracle.true_residual(U, b, to_np(x), KAPPA, L, BC, F) <= TOL
