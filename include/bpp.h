@@ -186,7 +186,7 @@ typedef struct {
                          bhat - Mhat x in double-float arithmetic (FP64 values held as
                          FP32 hi + lo pairs, ~48-bit significands, on the FP32 pipe),
                          while the solution, its accumulation, all norms and the final
-                         true residual stay FP64 */
+                         true residual stay FP64; ignored (FP64) when inner_prec is F64 */
 } bpp_solve_opts;
 
 /* Per right-hand side statistics of a solve. */

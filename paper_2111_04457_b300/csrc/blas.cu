@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_residual(OuterParams op) {
     }
 }
 
-template <int P>
+template <int P, bool SPLIT>
 __global__ void __launch_bounds__(BLAS_B) k_outer_down(OuterParams op) {
     using real = typename PT<P>::real;
     int s, tile;
@@ -416,13 +416,28 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_down(OuterParams op) {
     if (i >= d.g.Vh) return;
     const double sc = op.sc[s].scale;
     const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-    cx<double> r[12];
     cx<real> lo[12];
-    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, r);
+    if (SPLIT) {
+        // the defect's high parts carry all the accuracy the inner precision can hold
+        const float invf = (float)inv;
+        cx<df64> r[12];
+        Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, r);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) lo[k] = mkc<real>((real)(r[k].r * inv), (real)(r[k].i * inv));
+        for (int k = 0; k < 12; ++k) {
+            if (P == P64) lo[k] = mkc<real>((real)(r[k].r.to_double() * inv), (real)(r[k].i.to_double() * inv));
+            else lo[k] = mkc<real>((real)(r[k].r.hi * invf), (real)(r[k].i.hi * invf));
+        }
+    } else {
+        cx<double> r[12];
+        Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, r);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) lo[k] = mkc<real>((real)(r[k].r * inv), (real)(r[k].i * inv));
+    }
     Access<P>::store_spinor(sys_view<P>(op.b, op.sP[s]), i, lo);
 }
+
+__device__ __forceinline__ df64 to_df(float v) { return df64(v, 0.f); }
+__device__ __forceinline__ df64 to_df(double v) { return df64(v); }
 
 template <int P>
 __global__ void __launch_bounds__(BLAS_B) k_outer_acc(OuterParams op) {
@@ -441,15 +456,24 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_acc(OuterParams op) {
     for (int k = 0; k < 12; ++k) x[k] = x[k] + sc * mkc<double>((double)e[k].r, (double)e[k].i);
     Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, x);
     if (op.c) {
+        // the split copy takes the same update in double-float arithmetic (no
+        // FP64 conversions); it tracks x to ~1e-14 and only feeds the defects
         cx<df64> xs[12];
+        Access<P64S>::load_spinor(sys_view<P64S>(op.c, d), i, xs);
+        const df64 scd(sc);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) xs[k] = mkc(df64(x[k].r), df64(x[k].i));
+        for (int k = 0; k < 12; ++k) {
+            xs[k].r = fma(scd, to_df(e[k].r), xs[k].r);
+            xs[k].i = fma(scd, to_df(e[k].i), xs[k].i);
+        }
         Access<P64S>::store_spinor(sys_view<P64S>(op.c, d), i, xs);
     }
 }
 
-// r = bhat - m in FP64 from split-FP64 bhat (op.a) and m (op.b, may be null),
-// written to op.c, with ||r||^2 per system.  Split vectors share the FP64
+// r = bhat - m in double-float from split-FP64 bhat (op.a) and m (op.b, may
+// be null), written split to op.c, with ||r||^2 per system from the high parts
+// (FP32 per site, FP64 across sites: relative accuracy ~1e-7, ample for the
+// convergence test and the defect scale).  Split vectors share the FP64
 // vectors' offsets and strides (both 192 B per site).
 __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
     int s, tile;
@@ -459,16 +483,17 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
     double red[4] = {0, 0, 0, 0};
     if (i < d.g.Vh) {
         cx<df64> bh[12], m[12];
-        cx<double> r[12];
         Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, bh);
-        if (op.b) Access<P64S>::load_spinor(sys_view<P64S>(op.b, d), i, m);
+        if (op.b) {
+            Access<P64S>::load_spinor(sys_view<P64S>(op.b, d), i, m);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            r[k] = mkc(bh[k].r.to_double(), bh[k].i.to_double());
-            if (op.b) r[k] = r[k] - mkc(m[k].r.to_double(), m[k].i.to_double());
+            for (int k = 0; k < 12; ++k) bh[k] = bh[k] - m[k];
         }
-        Access<P64>::store_spinor(sys_view<P64>(op.c, d), i, r);
-        red[0] = norm12(r);
+        Access<P64S>::store_spinor(sys_view<P64S>(op.c, d), i, bh);
+        float n = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { n = fmaf(bh[k].r.hi, bh[k].r.hi, n); n = fmaf(bh[k].i.hi, bh[k].i.hi, n); }
+        red[0] = n;
     }
     BlasParams bp;
     bp.map = op.map;
@@ -480,6 +505,36 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
         op.sc[s].rr = tot[0];
         op.sc[s].scale = sqrt(tot[0]);
     }
+}
+
+// FP64 copy (hi + lo, exact) of a split-FP64 vector.
+__global__ void __launch_bounds__(BLAS_B) k_split_to_f64(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    cx<df64> v[12];
+    cx<double> w[12];
+    Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = mkc(v[k].r.to_double(), v[k].i.to_double());
+    Access<P64>::store_spinor(sys_view<P64>(op.b, d), i, w);
+}
+
+void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = b64.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    op.a = const_cast<char*>(xs);
+    op.b = x64;
+    op.c = nullptr;
+    op.sc = nullptr;
+    k_split_to_f64<<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
 }
 
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
@@ -518,7 +573,8 @@ void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& 
     BPP_CHECK_LAUNCH();
 }
 
-void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st) {
+void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st,
+                    bool split) {
     OuterParams op;
     op.s64 = b64.dev();
     op.sP = bP.dev();
@@ -528,9 +584,15 @@ void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo
     op.b = lo;
     op.c = nullptr;
     op.sc = const_cast<KScal*>(sc);
-    if (bP.prec == P64) k_outer_down<P64><<<nb, BLAS_B, 0, st>>>(op);
-    else if (bP.prec == P32) k_outer_down<P32><<<nb, BLAS_B, 0, st>>>(op);
-    else k_outer_down<P16><<<nb, BLAS_B, 0, st>>>(op);
+    if (split) {
+        if (bP.prec == P64) k_outer_down<P64, true><<<nb, BLAS_B, 0, st>>>(op);
+        else if (bP.prec == P32) k_outer_down<P32, true><<<nb, BLAS_B, 0, st>>>(op);
+        else k_outer_down<P16, true><<<nb, BLAS_B, 0, st>>>(op);
+    } else {
+        if (bP.prec == P64) k_outer_down<P64, false><<<nb, BLAS_B, 0, st>>>(op);
+        else if (bP.prec == P32) k_outer_down<P32, false><<<nb, BLAS_B, 0, st>>>(op);
+        else k_outer_down<P16, false><<<nb, BLAS_B, 0, st>>>(op);
+    }
     count_launch();
     BPP_CHECK_LAUNCH();
 }

@@ -63,15 +63,19 @@ void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cu
 // over the same systems):
 // r64 = bhat - r64 (r64 holds Mhat x on entry); sc.rr = ||r64||^2, sc.scale = ||r64||
 void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st);
-// lo = r64 / scale (converted to the inner precision)
-void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st);
+// lo = r / scale (converted to the inner precision); r is FP64, or split FP64
+// when split is set
+void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st,
+                    bool split = false);
 // x64 += scale * e (e in the inner precision); with x_split, also refresh the
 // split-FP64 copy of x (hi/lo FP32 pairs) used by the double-float defects
 void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* e, const KScal* sc, cudaStream_t st,
                       char* x_split = nullptr);
-// r64 = bhat_s - m_s from split-FP64 vectors (m_s may be null), in FP64, with
-// sc.rr = ||r64||^2 and sc.scale = ||r64||
-void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st);
+// r_s = bhat_s - m_s in double-float (m_s may be null), split-FP64 output, with
+// sc.rr = ||r_s||^2 and sc.scale = ||r_s||
+void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r_s, KScal* sc, RedBuf& rb, cudaStream_t st);
+// x64 = hi + lo of the split-FP64 vector xs (exact)
+void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st);
 // out = a * in + y (same precision), a per system given on the host
 void axpy_copy(const Batch& b, const char* in, char* out, cudaStream_t st);
 

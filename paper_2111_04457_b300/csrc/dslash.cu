@@ -228,8 +228,15 @@ template <> struct HopMaxThreads<P64> { static constexpr int value = 256; };
 template <> struct HopMaxThreads<P64S> { static constexpr int value = 256; };
 template <> struct HopMaxThreads<P16> { static constexpr int value = BPP_HOP16_MAXT; };
 
+// Minimum resident blocks per SM requested from the register allocator.
+#ifndef BPP_HOPDF_MINB
+#define BPP_HOPDF_MINB 2
+#endif
+template <int P> struct HopMinBlocks { static constexpr int value = 1; };
+template <> struct HopMinBlocks<P64S> { static constexpr int value = BPP_HOPDF_MINB; };
+
 template <int P, bool DAG, int MODE>
-__global__ void __launch_bounds__(HopMaxThreads<P>::value) k_hop(HopParams hp) {
+__global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::value) k_hop(HopParams hp) {
     using real = typename PT<P>::real;
     int s, tile;
     map_block(hp.map, s, tile);

@@ -72,7 +72,7 @@ struct Plan {
     bool split = false;                  // double-float defects (split-FP64 vectors)
     Batch b64, bP, b64s;
     Vec be, bo, bhat, xe, xo, r, tmpo;
-    Vec be_s, bo_s, bhat_s, xe_s, m_s, tmpo_s;
+    Vec be_s, bo_s, bhat_s, xe_s, m_s, tmpo_s, r_s;
     Vec w[9];
     RedBuf rb;
     DevBuf d64, dP, dloops;
@@ -127,7 +127,7 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
         batch_add(pl->b64s, *G[s], kappa[s], clover);
     }
     // evict least recently used plans beyond the count or byte budget
-    const size_t need = (split ? 13 : 7) * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes;
+    const size_t need = (split ? 14 : 7) * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes;
     for (;;) {
         size_t total = need;
         for (auto& p : g_plans) total += p->bytes;
@@ -144,7 +144,8 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     }
     for (Vec* v : {&pl->be, &pl->bo, &pl->bhat, &pl->xe, &pl->xo, &pl->r, &pl->tmpo}) alloc_vec(*pl, *v, pl->b64);
     if (split)
-        for (Vec* v : {&pl->be_s, &pl->bo_s, &pl->bhat_s, &pl->xe_s, &pl->m_s, &pl->tmpo_s}) alloc_vec(*pl, *v, pl->b64s);
+        for (Vec* v : {&pl->be_s, &pl->bo_s, &pl->bhat_s, &pl->xe_s, &pl->m_s, &pl->tmpo_s, &pl->r_s})
+            alloc_vec(*pl, *v, pl->b64s);
     for (auto& v : pl->w) alloc_vec(*pl, v, pl->bP);
     const int n = (int)G.size();
     pl->rb.persistent = true;
@@ -322,7 +323,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     BPP_REQUIRE(o.max_inner > 0 && o.max_outer > 0 && o.check_every > 0, BPP_ERR_INVALID_ARG, "iteration caps must be positive");
 
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    const bool split = o.outer_arith != 0;
+    // a plain FP64 solve (FP64 inner) stays FP64 throughout
+    const bool split = o.outer_arith != 0 && o.inner_prec != BPP_F64;
     Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, split, st);
     const Batch& b64 = pl.b64;
     const Batch& bP = pl.bP;
@@ -390,6 +392,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     std::vector<int> outer(n, 0), inner_it(n, 0), conv(n, 0), status(n, BPP_OK);
     std::vector<double> true_res(n, 0.0);
     bool have_full = false;
+    bool defect_split = false;   // the current defect lives in r_s (split) rather than r (FP64)
     auto read_rr = [&](std::vector<double>& dst) {
         read_scalars(pl.d64, h64, st);
         for (int s = 0; s < n; ++s) dst[s] = h64[s].rr;
@@ -397,7 +400,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     auto schur_residual = [&]() {
         if (split) {
             schur(b64s, clover, dag, pl.xe_s.p(), pl.m_s.p(), pl.tmpo_s.p(), st);
-            split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r.p(), sc64, pl.rb, st);
+            split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r_s.p(), sc64, pl.rb, st);
+            defect_split = true;
         } else {
             schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
             outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
@@ -406,8 +410,15 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         have_full = false;
     };
     auto full_residual = [&]() {
-        // x_o = A_oo^-1 (b_o + kappa H_oe x_e); De = A_ee x_e - kappa H_eo x_o; Do = A_oo x_o - kappa H_oe x_e
-        hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), st);
+        // x_o = A_oo^-1 (b_o + kappa H_oe x_e) (double-float when split, then its
+        // exact FP64 value); De = A_ee x_e - kappa H_eo x_o; Do = A_oo x_o - kappa H_oe x_e
+        // in FP64: the true residual of the returned x
+        if (split) {
+            hop(b64s, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe_s.p(), pl.tmpo_s.p(), pl.bo_s.p(), st);
+            split_to_f64(b64, pl.tmpo_s.p(), pl.xo.p(), st);
+        } else {
+            hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), st);
+        }
         hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xo.p(), pl.r.p(), pl.xe.p(), st);
         outer_residual(b64, pl.be.p(), pl.r.p(), sc64, pl.rb, st);
         read_rr(rr_e);
@@ -415,6 +426,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         outer_residual(b64, pl.bo.p(), pl.tmpo.p(), sc64, pl.rb, st);
         read_rr(rr_o);
         have_full = true;
+        defect_split = false;
         // outer_residual left the odd norm in the scalars; restore the even one
         // for the downcast of the next correction
         for (int s = 0; s < n; ++s) { h64[s].rr = rr_e[s]; h64[s].scale = std::sqrt(std::max(rr_e[s], 0.0)); }
@@ -422,7 +434,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     };
     if (x_zero) {
         if (split) {
-            split_residual(b64, pl.bhat_s.p(), nullptr, pl.r.p(), sc64, pl.rb, st);
+            split_residual(b64, pl.bhat_s.p(), nullptr, pl.r_s.p(), sc64, pl.rb, st);
+            defect_split = true;
         } else {
             BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
             outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
@@ -472,7 +485,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         }
         write_scalars(pl.d64, h64, st);
         write_scalars(pl.dP, hP, st);
-        outer_downcast(b64, bP, pl.r.p(), pl.w[0].p(), sc64, st);
+        outer_downcast(b64, bP, defect_split ? pl.r_s.p() : pl.r.p(), pl.w[0].p(), sc64, st, defect_split);
         inner_solve(pl, o, st);
         outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st, split ? pl.xe_s.p() : nullptr);
         bool all_predicted = true;
