@@ -3,19 +3,12 @@
 
 #include "blas.h"
 #include "kernels.h"
+#include "reduce.h"
 
 namespace bpp {
 
 constexpr int BLAS_B = 256;
 constexpr int BLAS_SPT = 4;   // sites per thread
-
-__host__ __device__ __forceinline__ double2 c2(double r, double i) { return make_double2(r, i); }
-__device__ __forceinline__ double2 cmul2(double2 a, double2 b) { return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
-    const double den = b.x * b.x + b.y * b.y;
-    return c2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
-}
-__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
 void RedBuf::ensure(int nblocks, int nsys, cudaStream_t st) {
     if (nblocks > cap_blocks) {
@@ -40,82 +33,6 @@ struct BlasParams {
     unsigned* tickets;
 };
 
-// Block-wide sum of NR doubles, then the last block of system s sums all the
-// system's block partials in block order; returns true in every thread of
-// that last block, with tot[] valid in thread 0.
-template <int NR>
-__device__ bool reduce_sys(const BlasParams& bp, int s, double v[NR], double tot[NR]) {
-    __shared__ double sh[32][NR];
-    __shared__ int last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        double a = v[k];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) sh[warp][k] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            double a = 0.0;
-            for (int w = 0; w < nw; ++w) a += sh[w][k];
-            bp.partials[(size_t)blockIdx.x * NR + k] = a;
-        }
-        __threadfence();
-        const int nb = bp.map.uniform ? bp.map.tiles_per_sys : bp.map.tile_start[s + 1] - bp.map.tile_start[s];
-        const unsigned t = atomicAdd(&bp.tickets[s], 1u);
-        last = (t == (unsigned)(nb - 1));
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    const int nb = bp.map.uniform ? bp.map.tiles_per_sys : bp.map.tile_start[s + 1] - bp.map.tile_start[s];
-    double a[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) a[k] = 0.0;
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-        const int blk = bp.map.uniform ? s + bp.map.nsys * t : bp.map.tile_start[s] + t;
-#pragma unroll
-        for (int k = 0; k < NR; ++k) a[k] += __ldcg(&bp.partials[(size_t)blk * NR + k]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        double b = a[k];
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
-        if (lane == 0) sh[warp][k] = b;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            double b = 0.0;
-            for (int w = 0; w < nw; ++w) b += sh[w][k];
-            tot[k] = b;
-        }
-        bp.tickets[s] = 0u;
-    }
-    return true;
-}
-
-template <class real>
-__device__ __forceinline__ void dot12(const cx<real> a[12], const cx<real> b[12], real& re, real& im) {
-    re = 0; im = 0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        re = fma(a[k].r, b[k].r, re); re = fma(a[k].i, b[k].i, re);
-        im = fma(a[k].r, b[k].i, im); im = fma(-a[k].i, b[k].r, im);
-    }
-}
-template <class real>
-__device__ __forceinline__ real norm12(const cx<real> a[12]) {
-    real n = 0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) { n = fma(a[k].r, a[k].r, n); n = fma(a[k].i, a[k].i, n); }
-    return n;
-}
-
 __device__ __forceinline__ void check_done(KScal& k) {
     if (!isfinite(k.rr)) { k.done = 1; k.status = 3; return; }
     if (k.rr <= k.tol2 * k.bb) { k.done = 1; return; }
@@ -125,7 +42,7 @@ __device__ __forceinline__ void check_done(KScal& k) {
 // The update and reduction terms of one site i of system d.
 template <int P, int OP>
 __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d, int i, double2 al, double2 om,
-                                          double2 be, double red[4]) {
+                                          double2 be, typename PT<P>::real red[4]) {
     using real = typename PT<P>::real;
     using A = Access<P>;
     cx<real> a[12], b[12], c[12];
@@ -137,7 +54,7 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
 #pragma unroll
         for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
         A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     } else if (OP == B_ALPHA) {
         real re, im;
         A::load_spinor(sys_view<P>(bp.v.rhat, d), i, a);
@@ -156,7 +73,7 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
         A::load_spinor(sys_view<P>(bp.v.t, d), i, a);
         A::load_spinor(sys_view<P>(bp.v.s, d), i, b);
         dot12(a, b, re, im);
-        red[0] += re; red[1] += im; red[2] += (double)norm12(a);
+        red[0] += re; red[1] += im; red[2] += norm12(a);
     } else if (OP == B_XR) {
         const cx<real> alr = mkc<real>((real)al.x, (real)al.y), omr = mkc<real>((real)om.x, (real)om.y);
         // x += alpha p + omega s
@@ -192,14 +109,14 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
 #pragma unroll
         for (int k = 0; k < 12; ++k) b[k] = mkc<real>(0, 0);
         A::store_spinor(sys_view<P>(bp.v.x, d), i, b);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     } else if (OP == B_CG_PZ) {
         A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
         A::store_spinor(sys_view<P>(bp.v.p, d), i, a);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     } else if (OP == B_CG_ALPHA) {
         A::load_spinor(sys_view<P>(bp.v.w, d), i, a);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     } else if (OP == B_CG_XR) {
         const real alr = (real)al.x;
         A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
@@ -212,13 +129,13 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
 #pragma unroll
         for (int k = 0; k < 12; ++k) a[k] = a[k] - alr * b[k];
         A::store_spinor(sys_view<P>(bp.v.r, d), i, a);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     } else if (OP == B_CG_BETA) {
         A::load_spinor(sys_view<P>(bp.v.z, d), i, a);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     } else if (OP == B_NORM2) {
         A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
-        red[0] += (double)norm12(a);
+        red[0] += norm12(a);
     }
 }
 
@@ -233,7 +150,8 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2) || !K->done;
     // scalars used by the update (read before any finalize of this launch)
     const double2 al = K->alpha, om = K->omega, be = K->beta;
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    using real = typename PT<P>::real;
+    real red[4] = {0, 0, 0, 0};
     if (active) {
         const int base = tile * (BLAS_SPT * BLAS_B) + threadIdx.x;
 #pragma unroll
@@ -246,7 +164,7 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     if (!HAS_RED) return;
     if (!active) return;   // whole system inactive: every block of it returns here
     double tot[4];
-    if (!reduce_sys<4>(bp, s, red, tot)) return;
+    if (!reduce_sys<4, real>(RedCtx{bp.map, bp.partials, bp.tickets}, s, red, tot)) return;
     if (threadIdx.x != 0) return;
     KScal& k = *K;
     if (OP == B_INIT_BICG) {
@@ -262,13 +180,9 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
         check_done(k);
         if (k.bb == 0.0) { k.done = 1; k.status = 0; }
     } else if (OP == B_ALPHA) {
-        k.rv = c2(tot[0], tot[1]);
-        if (cabs2(k.rv) == 0.0 || !isfinite(k.rv.x)) { k.status = 1; k.done = 1; k.alpha = c2(0, 0); }
-        else k.alpha = cdiv2(k.rho, k.rv);
+        finalize_alpha(k, tot[0], tot[1]);
     } else if (OP == B_OMEGA) {
-        k.ts = c2(tot[0], tot[1]);
-        k.tt = tot[2];
-        k.omega = k.tt > 0.0 ? c2(k.ts.x / k.tt, k.ts.y / k.tt) : c2(0.0, 0.0);
+        finalize_omega(k, tot[0], tot[1], tot[2]);
     } else if (OP == B_XR) {
         k.rr = tot[0];
         const double2 rho_new = c2(tot[1], tot[2]);
@@ -394,12 +308,8 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_residual(OuterParams op) {
         Access<P64>::store_spinor(sys_view<P64>(op.b, d), i, r);
         red[0] = norm12(r);
     }
-    BlasParams bp;
-    bp.map = op.map;
-    bp.partials = op.partials;
-    bp.tickets = op.tickets;
     double tot[4];
-    if (!reduce_sys<4>(bp, s, red, tot)) return;
+    if (!reduce_sys<4, double>(RedCtx{op.map, op.partials, op.tickets}, s, red, tot)) return;
     if (threadIdx.x == 0) {
         op.sc[s].rr = tot[0];
         op.sc[s].scale = sqrt(tot[0]);
@@ -480,7 +390,7 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
     map_block(op.map, s, tile);
     const SysDesc& d = op.s64[s];
     const int i = tile * blockDim.x + threadIdx.x;
-    double red[4] = {0, 0, 0, 0};
+    float red[4] = {0.f, 0.f, 0.f, 0.f};
     if (i < d.g.Vh) {
         cx<df64> bh[12], m[12];
         Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, bh);
@@ -495,12 +405,8 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
         for (int k = 0; k < 12; ++k) { n = fmaf(bh[k].r.hi, bh[k].r.hi, n); n = fmaf(bh[k].i.hi, bh[k].i.hi, n); }
         red[0] = n;
     }
-    BlasParams bp;
-    bp.map = op.map;
-    bp.partials = op.partials;
-    bp.tickets = op.tickets;
     double tot[4];
-    if (!reduce_sys<4>(bp, s, red, tot)) return;
+    if (!reduce_sys<4, float>(RedCtx{op.map, op.partials, op.tickets}, s, red, tot)) return;
     if (threadIdx.x == 0) {
         op.sc[s].rr = tot[0];
         op.sc[s].scale = sqrt(tot[0]);

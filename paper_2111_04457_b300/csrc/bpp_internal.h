@@ -427,14 +427,15 @@ struct DevBuf {
 };
 
 template <class Run>
-int tuned_block(const std::string& key, cudaStream_t s, Run run, bool may_tune = true, int max_block = 512) {
+int tuned_block(const std::string& key, cudaStream_t s, Run run, bool may_tune = true, int max_block = 512,
+                int min_block = 64) {
     int b = tune_lookup(key);
     if (b > 0) return b;
     if (!may_tune || capturing(s)) return max_block < 256 ? max_block : 256;
     static const int cand_all[] = {64, 128, 256, 512};
     std::vector<int> cand;
     for (int c : cand_all)
-        if (c <= max_block) cand.push_back(c);
+        if (c <= max_block && c >= min_block) cand.push_back(c);
     cudaEvent_t e0, e1;
     BPP_CUDA(cudaEventCreate(&e0));
     BPP_CUDA(cudaEventCreate(&e1));
