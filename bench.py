@@ -52,7 +52,14 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="host-driven inner loop instead of CUDA graphs")
     ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
                     help="solve: the timed mixed-precision solve (default); dslash: the hopping kernel alone")
+    ap.add_argument("--workload", default="wilson32",
+                    choices=["wilson32", "prop24", "uneven6", "clover48", "grad16"],
+                    help="wilson32: the default timed solve; prop24: 12 point sources on 24^3x48 in one "
+                         "batched solve; uneven6: six lattices of uneven size in one batched solve; "
+                         "clover48: Wilson-clover 48^3x96, 4 RHS, FP16 inner, with grad_b; "
+                         "grad16: FP64 solve + adjoint + link gradient on 16^3x32")
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "f64df"], help="precision for --mode dslash")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch for --mode dslash")
     return ap.parse_args()
 
 
@@ -414,7 +421,7 @@ def run_dslash(args, rank, world):
     g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
     Vh = L[0] * L[1] * L[2] * L[3] // 2
     dt = torch.complex128 if prec in (bpp.F64, bpp.F64DF) else torch.complex64
-    psi = torch.from_numpy(synth.gaussian_spinor(L, seed=2)[:Vh]).to(device=dev, dtype=dt)
+    psi = torch.from_numpy(synth.gaussian_spinor(L, seed=2, nrhs=args.nrhs)[:, :Vh]).to(device=dev, dtype=dt)
     for _ in range(args.warmup):
         bpp.dslash(g, psi, KAPPA, bpp.EVEN, prec)
     torch.cuda.synchronize()
@@ -436,9 +443,125 @@ def run_dslash(args, rank, world):
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / max(n, 1) * world,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
                       "data": "synthetic", "config": {"workload": f"even-odd Wilson hopping term {'x'.join(map(str, L))}",
-                                                      "lattice": list(L)},
-                      "frac_of_hbm": gbs / peak, "peak_kind": kind, "gsites_per_s": n * Vh / (ms / 1000.0) / 1e9}),
+                                                      "lattice": list(L), "nrhs": args.nrhs},
+                      "frac_of_hbm": gbs / peak, "peak_kind": kind,
+                      "gsites_per_s": n * Vh * args.nrhs / (ms / 1000.0) / 1e9}),
           flush=True)
+
+
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def run_workload(args, rank, world):
+    """The batched, clover and gradient workloads (one JSON line each)."""
+    import numpy as np
+    import torch
+
+    import paper_2111_04457_b300 as bpp
+    import synth
+    from paper_2111_04457_b300.autograd import solve_fn
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    steps, warm = args.steps, max(args.warmup, 1)
+    out = {"metric": METRIC, "unit": "GB/s", "n_gpus": world, "steps": steps, "warmup": warm,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+
+    def work_bytes(reset=True):
+        return sum(bpp.work_read(p, reset=reset)[1] for p in (0, 1, 2, 3))
+
+    if args.workload == "prop24":
+        L = (24, 24, 24, 48)
+        g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
+        b = torch.from_numpy(np.stack([synth.point_source(L, i) for i in range(12)])).to(dev)
+        x = torch.empty_like(b)
+        o = bpp.solve_opts(inner_prec=bpp.F32)
+        work_bytes()
+        ms, st = _timed(lambda: bpp.solve(g, b, KAPPA, 0.0, TOL, o, x=x)[1], steps, warm, stream)
+        by = work_bytes() / (steps + warm)
+        xs = torch.empty_like(b[0])
+        ms1, _ = _timed(lambda: [bpp.solve(g, b[i], KAPPA, 0.0, TOL, o, x=xs) for i in range(12)], 1, 1, stream)
+        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f32 inner, f64 outer",
+                   config={"workload": "12 spin-colour point sources on 24^3x48, one batched solve (FP32 inner, "
+                                       "FP64-class outer) to true resid 1e-10", "lattice": list(L), "rhs": 12},
+                   ms_per_rhs=ms / 12, ms_12_sequential_single_rhs=ms1, batching_speedup=ms1 / ms,
+                   true_resid_max=max(s["true_resid"] for s in st))
+    elif args.workload == "uneven6":
+        lats = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (20, 20, 20, 40), (24, 24, 24, 48)]
+        kap = synth.uniform_kappas(len(lats), seed=4)
+        gs = [bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L) for L in lats]
+        bs = [torch.from_numpy(synth.gaussian_spinor(L, seed=2 + i)).to(dev) for i, L in enumerate(lats)]
+        xs = [torch.empty_like(b) for b in bs]
+        o = bpp.solve_opts(inner_prec=bpp.F32)
+        work_bytes()
+        ms, st = _timed(lambda: bpp.solve_batch(gs, bs, kap, TOL, o, xs=xs)[1], steps, warm, stream)
+        by = work_bytes() / (steps + warm)
+        ms1, _ = _timed(lambda: [bpp.solve(gs[i], bs[i], kap[i], 0.0, TOL, o, x=xs[i]) for i in range(6)], 1, 1,
+                        stream)
+        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f32 inner, f64 outer",
+                   config={"workload": "6 lattices 8^4 12^4 16^4 16^3x32 20^3x40 24^3x48 (1204992 sites), kappa "
+                                       "U[0.10,0.12], one batched solve", "lattices": [list(L) for L in lats]},
+                   ms_6_sequential=ms1, batching_speedup=ms1 / ms, true_resid_max=max(s["true_resid"] for s in st))
+    elif args.workload == "clover48":
+        L = (48, 48, 48, 96)
+        csw = 1.0
+        g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.clover_build(KAPPA, csw)
+        torch.cuda.synchronize()
+        build_ms = 1000 * (time.perf_counter() - t0)
+        b = torch.from_numpy(synth.gaussian_spinor(L, seed=2, nrhs=4)).to(dev)
+        eta = torch.from_numpy(synth.gaussian_spinor(L, seed=3, nrhs=4)).to(dev)
+
+        def step():
+            bb = b.clone().requires_grad_(True)
+            xx = solve_fn(None, bb, L, KAPPA, csw=csw, tol=TOL, inner_prec=bpp.F16, gauge=g)
+            torch.vdot(eta.reshape(-1), xx.reshape(-1)).real.backward()
+            return bb.grad
+        work_bytes()
+        ms, lam = _timed(step, steps, warm, stream)
+        by = work_bytes() / (steps + warm)
+        Dl = bpp.dirac_apply(g, lam[0], KAPPA, csw, dagger=True)
+        res = (torch.linalg.vector_norm(eta[0] - Dl) / torch.linalg.vector_norm(eta[0])).item()
+        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f16-storage/f32 inner, f64 outer",
+                   config={"workload": "Wilson-clover c_SW=1 48^3x96, 4 Gaussian RHS: forward solve + adjoint "
+                                       "solve for grad_b (FP16 inner, FP64-class outer, true resid 1e-10)",
+                           "lattice": list(L), "rhs": 4, "csw": csw},
+                   clover_build_ms=build_ms, adjoint_true_resid_rhs0=res)
+    elif args.workload == "grad16":
+        L = (16, 16, 16, 32)
+        U = torch.from_numpy(synth.random_links(L, seed=1)).to(dev)
+        b = torch.from_numpy(synth.gaussian_spinor(L, seed=2)).to(dev)
+        eta = torch.from_numpy(synth.gaussian_spinor(L, seed=3)).to(dev)
+        g = bpp.Gauge(U, L)
+
+        def step():
+            UU = U.clone().requires_grad_(True)
+            bb = b.clone().requires_grad_(True)
+            xx = solve_fn(UU, bb, L, KAPPA, tol=1e-12, inner_prec=bpp.F64, gauge=g)
+            torch.vdot(eta.reshape(-1), xx.reshape(-1)).real.backward()
+            return UU.grad
+        work_bytes()
+        ms, gU = _timed(step, steps, warm, stream)
+        by = work_bytes() / (steps + warm)
+        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f64",
+                   config={"workload": "L = Re<eta, D^-1 b> on 16^3x32 FP64: forward solve, adjoint solve, "
+                                       "recomputed x, link-gradient kernel", "lattice": list(L)})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def main():
@@ -448,6 +571,8 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "dslash":
         run_dslash(args, rank, world)
+    elif args.workload != "wilson32":
+        run_workload(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -254,7 +254,8 @@ int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int re
 /* Reads (and with reset != 0 clears) the work done by the even-odd hopping
  * kernels of precision prec since load: launches and algorithmic bytes (per
  * output site: 8 links + input and output spinor, + the xpay operand and
- * clover blocks of fused epilogues).  Graph-executed iterations are credited
+ * clover blocks of fused epilogues; right-hand sides that share a gauge field
+ * count its links once per launch).  Graph-executed iterations are credited
  * per system for the iterations that system was active.  Does not synchronise. */
 int bpp_work_read(int prec, int64_t* launches, double* bytes, int reset);
 

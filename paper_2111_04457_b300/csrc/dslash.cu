@@ -373,17 +373,27 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
         k_hop<P, DAG, MODE><<<nb, B, 0, st>>>(hp);
     };
     const int B = tuned_block(key, st, run, out != y && out != in, HopMaxThreads<P>::value);
-    double sites = 0;
-    for (auto& sd : b.sys) sites += sd.g.Vh;
-    const double bps = hop_bytes_per_site(P, MODE);
-    ProfScope prof(P, sites * bps, st);
+    // algorithmic bytes: systems that share a gauge field (the right-hand sides
+    // of one lattice) read its links once per launch
+    double sites = 0, bytes = 0;
+    const double bps = hop_bytes_per_site(P, MODE), lbytes = 8.0 * link_bytes(P);
+    std::vector<double> per_sys(b.nsys());
+    for (int s = 0; s < b.nsys(); ++s) {
+        bool first = true;
+        for (int r = 0; r < s; ++r)
+            if (b.sys[r].U[0][0].data == b.sys[s].U[0][0].data) first = false;
+        per_sys[s] = b.sys[s].g.Vh * (first ? bps : bps - lbytes);
+        sites += b.sys[s].g.Vh;
+        bytes += per_sys[s];
+    }
+    ProfScope prof(P, bytes, st);
     run(B);
     count_launch();
     BPP_CHECK_LAUNCH();
     if (thread_capturing()) {
-        for (int s = 0; s < b.nsys(); ++s) capture_hop_work(P, s, b.sys[s].g.Vh * bps);
+        for (int s = 0; s < b.nsys(); ++s) capture_hop_work(P, s, per_sys[s]);
     } else {
-        add_hop_work(P, 1, sites * bps);
+        add_hop_work(P, 1, bytes);
     }
 }
 
