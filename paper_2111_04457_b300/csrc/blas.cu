@@ -443,6 +443,93 @@ void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st) 
     BPP_CHECK_LAUNCH();
 }
 
+// Copy of an inner-precision vector (op.a, batch sP) as FP32 (op.b, batch s64
+// holds the FP32 batch here).
+template <int PIN>
+__global__ void __launch_bounds__(BLAS_B) k_to_f32(OuterParams op) {
+    using real = typename PT<PIN>::real;
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    cx<real> v[12];
+    cx<float> w[12];
+    Access<PIN>::load_spinor(sys_view<PIN>(op.a, op.sP[s]), i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = mkc((float)v[k].r, (float)v[k].i);
+    Access<P32>::store_spinor(sys_view<P32>(op.b, d), i, w);
+}
+
+void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b32.dev();
+    op.sP = bin.dev();
+    int nb = 0;
+    op.map = block_map(b32, BLAS_B, nb);
+    op.a = const_cast<char*>(in);
+    op.b = out;
+    op.c = nullptr;
+    op.sc = nullptr;
+    if (bin.prec == P16) k_to_f32<P16><<<nb, BLAS_B, 0, st>>>(op);
+    else if (bin.prec == P32) k_to_f32<P32><<<nb, BLAS_B, 0, st>>>(op);
+    else throw Error(BPP_ERR_UNSUPPORTED, "to_f32 takes FP16 or FP32 vectors");
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+// Recursive defect update r_s -= scale * m (m = Mhat e in FP32, op.b with the
+// FP32 batch in sP), double-float, with ||r_s||^2 from the high parts.
+__global__ void __launch_bounds__(BLAS_B) k_defect_update(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    const df64 sc = df64(-op.sc[s].scale);
+    float red[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < d.g.Vh) {
+        cx<df64> r[12];
+        cx<float> m[12];
+        Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, r);
+        Access<P32>::load_spinor(sys_view<P32>(op.b, op.sP[s]), i, m);
+        float n = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            r[k].r = fma(sc, df64(m[k].r, 0.f), r[k].r);
+            r[k].i = fma(sc, df64(m[k].i, 0.f), r[k].i);
+            n = fmaf(r[k].r.hi, r[k].r.hi, n);
+            n = fmaf(r[k].i.hi, r[k].i.hi, n);
+        }
+        Access<P64S>::store_spinor(sys_view<P64S>(op.a, d), i, r);
+        red[0] = n;
+    }
+    double tot[4];
+    if (!reduce_sys<4, float>(RedCtx{op.map, op.partials, op.tickets}, s, red, tot)) return;
+    if (threadIdx.x == 0) {
+        op.sc[s].rr = tot[0];
+        op.sc[s].scale = sqrt(tot[0]);
+    }
+}
+
+void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m32, KScal* sc, RedBuf& rb,
+                   cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = b32.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    rb.ensure(nb, b64.nsys(), st);
+    op.a = r_s;
+    op.b = const_cast<char*>(m32);
+    op.c = nullptr;
+    op.sc = sc;
+    op.partials = rb.partials.as<double>();
+    op.tickets = rb.tickets.as<unsigned>();
+    k_defect_update<<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
     OuterParams op;
     op.s64 = b64.dev();

@@ -74,6 +74,12 @@ void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* 
 // r_s = bhat_s - m_s in double-float (m_s may be null), split-FP64 output, with
 // sc.rr = ||r_s||^2 and sc.scale = ||r_s||
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r_s, KScal* sc, RedBuf& rb, cudaStream_t st);
+// out (FP32, batch b32) = in (FP16 or FP32, batch bin)
+void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaStream_t st);
+// r_s -= scale * m32 (split-FP64 defect, FP32 m = Mhat e), with the new
+// ||r_s||^2 and ||r_s|| in the scalars (scale is read before it is replaced)
+void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m32, KScal* sc, RedBuf& rb,
+                   cudaStream_t st);
 // x64 = hi + lo of the split-FP64 vector xs (exact)
 void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st);
 // out = a * in + y (same precision), a per system given on the host

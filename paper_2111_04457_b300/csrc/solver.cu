@@ -70,7 +70,9 @@ struct Plan {
     bool clover = false;
     int prec = P32, solver = BPP_BICGSTAB;
     bool split = false;                  // double-float defects (split-FP64 vectors)
-    Batch b64, bP, b64s;
+    bool reliable = false;               // FP32 recursive defect updates between recomputations
+    Batch b64, bP, b64s, b32;
+    Vec e32, m32, tmp32;
     Vec be, bo, bhat, xe, xo, r, tmpo;
     Vec be_s, bo_s, bhat_s, xe_s, m_s, tmpo_s, r_s;
     Vec w[9];
@@ -121,13 +123,17 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     pl->b64.prec = P64;
     pl->bP.prec = prec;
     pl->b64s.prec = P64S;
+    pl->b32.prec = P32;
+    pl->reliable = split && prec == P16;
     for (size_t s = 0; s < G.size(); ++s) {
         batch_add(pl->b64, *G[s], kappa[s], clover);
         batch_add(pl->bP, *G[s], kappa[s], clover);
         batch_add(pl->b64s, *G[s], kappa[s], clover);
+        batch_add(pl->b32, *G[s], kappa[s], clover);
     }
     // evict least recently used plans beyond the count or byte budget
-    const size_t need = (split ? 14 : 7) * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes;
+    const size_t need = (split ? 14 : 7) * pl->b64.vec_bytes + 9 * pl->bP.vec_bytes +
+                        (pl->reliable ? 3 * pl->b32.vec_bytes : 0);
     for (;;) {
         size_t total = need;
         for (auto& p : g_plans) total += p->bytes;
@@ -138,7 +144,7 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
         BPP_CUDA(cudaDeviceSynchronize());
         g_plans.erase(g_plans.begin() + lru);
     }
-    for (Batch* b : {&pl->b64, &pl->bP, &pl->b64s}) {
+    for (Batch* b : {&pl->b64, &pl->bP, &pl->b64s, &pl->b32}) {
         b->dsys.alloc_persistent(b->sys.size() * sizeof(SysDesc));
         BPP_CUDA(cudaMemcpy(b->dsys.p, b->sys.data(), b->sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
     }
@@ -146,6 +152,8 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     if (split)
         for (Vec* v : {&pl->be_s, &pl->bo_s, &pl->bhat_s, &pl->xe_s, &pl->m_s, &pl->tmpo_s, &pl->r_s})
             alloc_vec(*pl, *v, pl->b64s);
+    if (pl->reliable)
+        for (Vec* v : {&pl->e32, &pl->m32, &pl->tmp32}) alloc_vec(*pl, *v, pl->b32);
     for (auto& v : pl->w) alloc_vec(*pl, v, pl->bP);
     const int n = (int)G.size();
     pl->rb.persistent = true;
@@ -393,11 +401,16 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     std::vector<double> true_res(n, 0.0);
     bool have_full = false;
     bool defect_split = false;   // the current defect lives in r_s (split) rather than r (FP64)
+    // Accumulated error of FP32 recursive defect updates since the last
+    // recomputation, estimated as 4 * 2^-24 * ||Mhat e|| * scale per update.
+    std::vector<double> drift(n, 0.0);
+    const double eps32 = 4.0 * 5.96e-8;
     auto read_rr = [&](std::vector<double>& dst) {
         read_scalars(pl.d64, h64, st);
         for (int s = 0; s < n; ++s) dst[s] = h64[s].rr;
     };
     auto schur_residual = [&]() {
+        std::fill(drift.begin(), drift.end(), 0.0);
         if (split) {
             schur(b64s, clover, dag, pl.xe_s.p(), pl.m_s.p(), pl.tmpo_s.p(), st);
             split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r_s.p(), sc64, pl.rb, st);
@@ -497,8 +510,27 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
             pred[s] = std::sqrt(std::max(rr_e[s], 0.0)) * inner_rel;
             if (!(pred[s] <= 0.5 * target[s] * std::sqrt(bnorm2[s]))) all_predicted = false;
         }
-        if (all_predicted) full_residual();
-        else schur_residual();
+        // recursive FP32 update of the defect when its accumulated error stays
+        // below 1% of the defect it predicts; otherwise recompute it
+        bool reliable_ok = pl.reliable && defect_split;
+        for (int s = 0; s < n; ++s) {
+            if (!active[s]) continue;
+            const double step = eps32 * std::sqrt(std::max(rr_e[s], 0.0));
+            if (!(drift[s] + step <= 0.01 * pred[s])) reliable_ok = false;
+        }
+        if (all_predicted) {
+            full_residual();
+        } else if (reliable_ok) {
+            to_f32(bP, pl.b32, pl.w[1].p(), pl.e32.p(), st);
+            schur(pl.b32, clover, dag, pl.e32.p(), pl.m32.p(), pl.tmp32.p(), st);
+            defect_update(b64, pl.b32, pl.r_s.p(), pl.m32.p(), sc64, pl.rb, st);
+            for (int s = 0; s < n; ++s)
+                if (active[s]) drift[s] += eps32 * std::sqrt(std::max(rr_e[s], 0.0));
+            read_rr(rr_e);
+            have_full = false;
+        } else {
+            schur_residual();
+        }
     }
     if (!have_full) {
         full_residual();
