@@ -27,7 +27,7 @@
  *     four-plaquette clover leaf Q.
  *   - Canonical spinor layout: complex [nrhs][V][4][3] (spin, then colour),
  *     lexicographic sites.  Half-lattice ("even-odd") fields hold the Vh = V/2
- *     sites of one parity in lexicographic order.  L1 must be even.
+ *     sites of one parity in lexicographic order.  Every extent must be even.
  *   - Canonical link layout: complex128 [4][V][3][3], row-major U_mu(x)[a][b].
  *   - The complex element type of a canonical field is complex128 for BPP_F64
  *     and BPP_F64DF and complex64 for BPP_F32 and BPP_F16 (FP16 is a storage
@@ -71,7 +71,8 @@ typedef enum { BPP_F64 = 0, BPP_F32 = 1, BPP_F16 = 2, BPP_F64DF = 3 } bpp_prec;
 typedef enum { BPP_EVEN = 0, BPP_ODD = 1, BPP_FULL = 2 } bpp_parity;
 typedef enum { BPP_BICGSTAB = 0, BPP_CGNR = 1 } bpp_solver;
 
-/* Lattice extents L[mu] (L[0] even, every L[mu] >= 2) and boundary signs bc[mu]
+/* Lattice extents L[mu] (every L[mu] even and >= 2: the even-odd decomposition
+ * needs neighbours of opposite parity) and boundary signs bc[mu]
  * in {+1, -1}; the paper's workloads use bc = {1, 1, 1, -1}. */
 typedef struct {
     int L[4];
@@ -79,7 +80,7 @@ typedef struct {
 } bpp_lattice;
 
 /* Opaque gauge handle: owns device copies of the links in the internal
- * even-odd structure-of-arrays layout in all three precisions, plus the clover
+ * even-odd structure-of-arrays layout in all four storage formats, plus the clover
  * term and its inverse once bpp_clover_build() ran. */
 typedef struct bpp_gauge_s* bpp_gauge;
 
@@ -93,7 +94,7 @@ int bpp_last_error(char* buf, size_t n);
 /* Gauge field U_mu(x) of Eq. (1) (Sec. 2: "link variable U_mu(x) in SU(3)").
  * U_lex: complex128 [4][V][3][3] in device or host memory (detected); copied,
  * the caller keeps ownership.  Synchronises `stream` before returning.
- * Errors: INVALID_ARG (NULL pointer, odd L[0], L[mu] < 2, bc not +-1),
+ * Errors: INVALID_ARG (NULL pointer, odd L[mu], L[mu] < 2, bc not +-1),
  * OOM, CUDA. */
 int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream stream, bpp_gauge* out);
 

@@ -95,7 +95,9 @@ int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream strea
             BPP_REQUIRE(lat->L[mu] >= 2, BPP_ERR_INVALID_ARG, "every L[mu] must be >= 2");
             BPP_REQUIRE(lat->bc[mu] == 1 || lat->bc[mu] == -1, BPP_ERR_INVALID_ARG, "bc[mu] must be +1 or -1");
         }
-        BPP_REQUIRE(lat->L[0] % 2 == 0, BPP_ERR_INVALID_ARG, "L[0] must be even");
+        // even-odd preconditioning needs a bipartite lattice: every extent even
+        for (int mu = 0; mu < 4; ++mu)
+            BPP_REQUIRE(lat->L[mu] % 2 == 0, BPP_ERR_INVALID_ARG, "every L[mu] must be even (even-odd decomposition)");
         const int64_t V = (int64_t)lat->L[0] * lat->L[1] * lat->L[2] * lat->L[3];
         BPP_REQUIRE(V / 2 < (int64_t)1 << 30, BPP_ERR_INVALID_ARG, "lattice too large");
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

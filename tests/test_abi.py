@@ -40,3 +40,19 @@ def test_version_and_error_without_gpu():
     assert rc == -1
     assert bpp._lib.bpp_last_error(buf, 256) == -1
     assert b"NULL" in buf.value
+
+
+def test_gauge_create_rejects_bad_lattices_before_touching_the_gpu():
+    import paper_2111_04457_b300 as bpp
+    lib = bpp._lib
+    h = ctypes.c_void_p()
+    dummy = ctypes.create_string_buffer(16)
+    for L, bc in [((4, 3, 4, 4), (1, 1, 1, -1)),     # odd extent: not bipartite
+                  ((3, 4, 4, 4), (1, 1, 1, -1)),
+                  ((4, 4, 4, 0), (1, 1, 1, -1)),
+                  ((4, 4, 4, 4), (1, 1, 1, 2))]:       # bc must be +-1
+        lat = bpp._Lattice((ctypes.c_int * 4)(*L), (ctypes.c_int * 4)(*bc))
+        rc = lib.bpp_gauge_create(ctypes.byref(lat), dummy, None, ctypes.byref(h))
+        assert rc == -1, (L, bc)
+    rc = lib.bpp_gauge_create(None, dummy, None, ctypes.byref(h))
+    assert rc == -1
