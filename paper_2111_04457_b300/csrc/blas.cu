@@ -530,6 +530,57 @@ void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m3
     BPP_CHECK_LAUNCH();
 }
 
+// v *= scale of the system (FP64, in place).
+__global__ void __launch_bounds__(BLAS_B) k_scale_f64(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    const double f = op.sc[s].scale;
+    cx<double> v[12];
+    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = f * v[k];
+    Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
+}
+
+// split-FP64 copy (op.b) of an FP64 vector (op.a).
+__global__ void __launch_bounds__(BLAS_B) k_f64_to_split(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    cx<double> v[12];
+    cx<df64> w[12];
+    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = mkc(df64(v[k].r), df64(v[k].i));
+    Access<P64S>::store_spinor(sys_view<P64S>(op.b, d), i, w);
+}
+
+static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, char* b, KScal* sc, cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = b64.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    op.a = a;
+    op.b = b;
+    op.c = nullptr;
+    op.sc = sc;
+    kern<<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
+void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) { launch_outer(k_scale_f64, b64, v, nullptr, sc, st); }
+
+void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st) {
+    launch_outer(k_f64_to_split, b64, const_cast<char*>(in), out, nullptr, st);
+}
+
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
     OuterParams op;
     op.s64 = b64.dev();

@@ -74,6 +74,10 @@ void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* 
 // r_s = bhat_s - m_s in double-float (m_s may be null), split-FP64 output, with
 // sc.rr = ||r_s||^2 and sc.scale = ||r_s||
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r_s, KScal* sc, RedBuf& rb, cudaStream_t st);
+// v *= sc[s].scale per system (FP64, in place)
+void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st);
+// out = split-FP64 copy of the FP64 vector in
+void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st);
 // out (FP32, batch b32) = in (FP16 or FP32, batch bin)
 void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaStream_t st);
 // r_s -= scale * m32 (split-FP64 defect, FP32 m = Mhat e), with the new

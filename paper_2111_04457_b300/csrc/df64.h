@@ -21,9 +21,26 @@ struct df64 {
     __host__ __device__ df64() {}
     __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ df64(int v) : hi((float)v), lo(0.f) {}
+    // Split of an FP64 value with integer operations (the FP64 pipe is slow on
+    // this GPU): hi = v truncated to 24 significant bits (exact in FP32), lo =
+    // the remaining 29 bits rounded once to FP32, so hi + lo = v to 2^-48.
+    // Zero, and magnitudes outside 2^-74 .. 2^100 (where 2^(e - 1075) would not
+    // be a normal FP32 number), take the FP64 route.
     __device__ explicit df64(double v) {
-        hi = __double2float_rn(v);
-        lo = __double2float_rn(v - (double)hi);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const int e = (int)((b >> 52) & 0x7FF);
+        if ((b << 1) == 0ULL) {
+            hi = lo = __uint_as_float((unsigned)(b >> 32));   // +-0
+        } else if (e < 949 || e > 1023 + 100) {
+            hi = __double2float_rn(v);
+            lo = __double2float_rn(v - (double)hi);
+        } else {
+            const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+            hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+            const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);   // 2^(e - 1075)
+            const float l = __uint2float_rn((unsigned)(b & 0x1FFFFFFFu)) * scale;
+            lo = sign ? -l : l;
+        }
     }
     __device__ double to_double() const { return (double)hi + (double)lo; }
 };

@@ -341,13 +341,42 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     std::vector<KScal>& hP = pl.hP;
     pl.rb.ensure(1, n, st);   // tickets
 
-    // b -> even/odd FP64 (gamma5 b for the adjoint solve), and split FP64
+    // b -> even/odd FP64 (gamma5 b for the adjoint solve)
     const Batch& b64s = pl.b64s;
-    for (int s = 0; s < n; ++s) {
-        full_to_eo(b64, s, 1, b_canon[s], 1, 0, pl.be.p(), pl.bo.p(), o.dagger ? 1 : 0, st);
-        if (split) full_to_eo(b64s, s, 1, b_canon[s], 1, 0, pl.be_s.p(), pl.bo_s.p(), o.dagger ? 1 : 0, st);
-    }
+    for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, b_canon[s], 1, 0, pl.be.p(), pl.bo.p(), o.dagger ? 1 : 0, st);
     const int dag = 0;
+    // ||b||^2 = ||b_e||^2 + ||b_o||^2
+    std::vector<double> bnorm2(n), bscale(n, 1.0);
+    {
+        BlasVecs v;
+        v.x = pl.be.p();
+        blas(b64, B_NORM2, v, sc64, pl.rb, st);
+        read_scalars(pl.d64, h64, st);
+        for (int s = 0; s < n; ++s) bnorm2[s] = h64[s].bb;
+        v.x = pl.bo.p();
+        blas(b64, B_NORM2, v, sc64, pl.rb, st);
+        read_scalars(pl.d64, h64, st);
+        for (int s = 0; s < n; ++s) bnorm2[s] += h64[s].bb;
+    }
+    for (int s = 0; s < n; ++s)
+        BPP_REQUIRE(std::isfinite(bnorm2[s]), BPP_ERR_NONFINITE, "non-finite right-hand side");
+    // The system is linear: solve D x' = b / ||b|| and return x = ||b|| x'.  The
+    // normalised right-hand side keeps every split-FP64 value inside the FP32
+    // exponent range whatever the scale of b.
+    for (int s = 0; s < n; ++s) {
+        if (bnorm2[s] > 0.0) {
+            bscale[s] = std::sqrt(bnorm2[s]);
+            bnorm2[s] = 1.0;
+        }
+        h64[s].scale = 1.0 / bscale[s];
+    }
+    write_scalars(pl.d64, h64, st);
+    scale_f64(b64, pl.be.p(), sc64, st);
+    scale_f64(b64, pl.bo.p(), sc64, st);
+    if (split) {
+        f64_to_split(b64, pl.be.p(), pl.be_s.p(), st);
+        f64_to_split(b64, pl.bo.p(), pl.bo_s.p(), st);
+    }
     // bhat = b_e + kappa H_eo A_oo^-1 b_o (double-float when split)
     {
         const Batch& bb = split ? b64s : b64;
@@ -362,29 +391,13 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
             hop(bb, 0, dag, HOP_XPAY, +1.0, bo_, bh_, be_, st);
         }
     }
-    // norms: ||b||^2 = ||b_e||^2 + ||b_o||^2
-    std::vector<double> bnorm2(n);
-    {
-        BlasVecs v;
-        v.x = pl.be.p();
-        blas(b64, B_NORM2, v, sc64, pl.rb, st);
-        read_scalars(pl.d64, h64, st);
-        for (int s = 0; s < n; ++s) bnorm2[s] = h64[s].bb;
-        v.x = pl.bo.p();
-        blas(b64, B_NORM2, v, sc64, pl.rb, st);
-        read_scalars(pl.d64, h64, st);
-        for (int s = 0; s < n; ++s) bnorm2[s] += h64[s].bb;
-    }
-    for (int s = 0; s < n; ++s)
-        BPP_REQUIRE(std::isfinite(bnorm2[s]), BPP_ERR_NONFINITE, "non-finite right-hand side");
 
-    // initial guess
+    // initial guess (scaled like b)
     bool x_zero = !o.use_x0;
     if (o.use_x0) {
-        for (int s = 0; s < n; ++s) {
-            full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
-            if (split) full_to_eo(b64s, s, 1, x_canon[s], 1, 0, pl.xe_s.p(), pl.tmpo_s.p(), o.dagger ? 1 : 0, st);
-        }
+        for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
+        scale_f64(b64, pl.xe.p(), sc64, st);
+        if (split) f64_to_split(b64, pl.xe.p(), pl.xe_s.p(), st);
     } else {
         BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
         if (split) BPP_CUDA(cudaMemsetAsync(pl.xe_s.p(), 0, b64s.vec_bytes, st));
@@ -543,6 +556,11 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         for (int s = 0; s < n; ++s)
             if (status[s] == BPP_OK && bnorm2[s] > 0.0) true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);
     }
+    // x = ||b|| x'
+    for (int s = 0; s < n; ++s) h64[s].scale = bscale[s];
+    write_scalars(pl.d64, h64, st);
+    scale_f64(b64, pl.xe.p(), sc64, st);
+    scale_f64(b64, pl.xo.p(), sc64, st);
     for (int s = 0; s < n; ++s) eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st);
     BPP_CUDA(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

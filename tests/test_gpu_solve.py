@@ -119,3 +119,33 @@ def test_solve_outer_arithmetic(inner, outer_df64, csw):
     b = synth.gaussian_spinor(L, seed=2)
     x, st = bpp.solve(g, to_dev(b), KAPPA, csw, TOL, bpp.solve_opts(inner_prec=inner, outer_df64=outer_df64))
     assert oracle.true_residual(U, b, to_np(x), KAPPA, L, BC, F) <= TOL
+
+
+@pytest.mark.parametrize("scale", [1e-40, 1e-20, 1e20, 1e60])
+@pytest.mark.parametrize("inner", [1, 2])
+def test_solve_any_rhs_scale(scale, inner):
+    """The solver normalises b, so the double-float outer loop (FP32 exponent
+    range) works for right-hand sides of any magnitude; x scales with b."""
+    bpp = lib()
+    L = (4, 4, 4, 6)
+    g, U = gauge(L)
+    b = synth.gaussian_spinor(L, seed=2)
+    x1, _ = bpp.solve(g, to_dev(b), KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner))
+    xs, st = bpp.solve(g, to_dev(b * scale), KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner))
+    assert st[0]["converged"] == 1
+    assert oracle.true_residual(U, b * scale, to_np(xs), KAPPA, L, BC) <= TOL
+    assert rel_err(to_np(xs) / scale, to_np(x1)) <= 1e-9
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-20, 1e20])
+def test_dslash_f64df_scales(scale):
+    """Double-float dslash across magnitudes (integer split fast path and the
+    FP64 route for small values)."""
+    bpp = lib()
+    L = (4, 4, 4, 6)
+    g, U = gauge(L)
+    Vh = oracle.volume(L) // 2
+    psi = synth.gaussian_spinor(L, seed=2)[:Vh] * scale
+    ref = oracle.hop_eo(U, psi, KAPPA, L, 0, BC)
+    out = to_np(bpp.dslash(g, to_dev(psi), KAPPA, 0, bpp.F64DF))
+    assert rel_err(out, ref) <= 1e-12
