@@ -180,11 +180,9 @@ __device__ __forceinline__ void decode(const Raw<P16>& r, cx<float> psi[12], cx<
 
 // One hop term: decode, project with (1 + S gamma_MU), colour-multiply
 // (U or U^dag), reconstruct into acc.
-template <int P, int MU, int S, bool BACK>
-__device__ __forceinline__ void hop_term(cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
-    using real = typename PT<P>::real;
-    cx<real> psi[12], h[6], g[6], u[9];
-    decode(raw, psi, u);
+template <int MU, int S, bool BACK, class real>
+__device__ __forceinline__ void hop_term_dec(cx<real> acc[12], const cx<real> psi[12], const cx<real> u[9], bool flip) {
+    cx<real> h[6], g[6];
     project<MU, S>(psi, h);
     if (flip) {
 #pragma unroll
@@ -192,6 +190,30 @@ __device__ __forceinline__ void hop_term(cx<typename PT<P>::real> acc[12], const
     }
     link_mul<BACK>(u, h, g);
     reconstruct<MU, S>(acc, g);
+}
+
+template <int P, int MU, int S, bool BACK>
+__device__ __forceinline__ void hop_term(cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
+    using real = typename PT<P>::real;
+    cx<real> psi[12], u[9];
+    decode(raw, psi, u);
+    hop_term_dec<MU, S, BACK>(acc, psi, u, flip);
+}
+
+// Direction d with decoded operands (see hop_term_d).
+template <int SF, class real>
+__device__ __forceinline__ void hop_term_dec_d(int d, cx<real> acc[12], const cx<real> psi[12], const cx<real> u[9],
+                                               bool flip) {
+    switch (d) {
+        case 0: hop_term_dec<0, SF, false>(acc, psi, u, flip); break;
+        case 1: hop_term_dec<0, -SF, true>(acc, psi, u, flip); break;
+        case 2: hop_term_dec<1, SF, false>(acc, psi, u, flip); break;
+        case 3: hop_term_dec<1, -SF, true>(acc, psi, u, flip); break;
+        case 4: hop_term_dec<2, SF, false>(acc, psi, u, flip); break;
+        case 5: hop_term_dec<2, -SF, true>(acc, psi, u, flip); break;
+        case 6: hop_term_dec<3, SF, false>(acc, psi, u, flip); break;
+        default: hop_term_dec<3, -SF, true>(acc, psi, u, flip); break;
+    }
 }
 
 // Direction d = 2 mu + (0 forward, 1 backward); SF is the forward projector sign.
@@ -221,6 +243,44 @@ __device__ __forceinline__ void hop_term_d(int d, cx<typename PT<P>::real> acc[1
 template <int P> struct HopPrefetch { static constexpr bool value = BPP_HOP_PREFETCH != 0; };
 template <> struct HopPrefetch<P64> { static constexpr bool value = false; };
 template <> struct HopPrefetch<P64S> { static constexpr bool value = false; };
+
+// Neighbour half-lattice indices jn, link indices ju and boundary flips of the
+// 8 hops of output site i (coordinates x1..x4, row r = i / Lh).
+__device__ __forceinline__ void hop_neighbours(const Geom& g, int i, int x1, int x1h, int r, int x2, int x3, int x4,
+                                               int jn[8], int ju[8], bool flip[8]) {
+    {
+        const bool wf = x1 == g.L[0] - 1, wb = x1 == 0;
+        jn[0] = ((wf ? 0 : x1 + 1) >> 1) + g.Lh * r;
+        jn[1] = ((wb ? g.L[0] - 1 : x1 - 1) >> 1) + g.Lh * r;
+        flip[0] = wf && g.bc[0] < 0;
+        flip[1] = wb && g.bc[0] < 0;
+    }
+    {
+        const bool wf = x2 == g.L[1] - 1, wb = x2 == 0;
+        jn[2] = x1h + g.Lh * (wf ? r - (g.L[1] - 1) : r + 1);
+        jn[3] = x1h + g.Lh * (wb ? r + (g.L[1] - 1) : r - 1);
+        flip[2] = wf && g.bc[1] < 0;
+        flip[3] = wb && g.bc[1] < 0;
+    }
+    {
+        const int st = g.L[1];
+        const bool wf = x3 == g.L[2] - 1, wb = x3 == 0;
+        jn[4] = x1h + g.Lh * (wf ? r - (g.L[2] - 1) * st : r + st);
+        jn[5] = x1h + g.Lh * (wb ? r + (g.L[2] - 1) * st : r - st);
+        flip[4] = wf && g.bc[2] < 0;
+        flip[5] = wb && g.bc[2] < 0;
+    }
+    {
+        const int st = g.L[1] * g.L[2];
+        const bool wf = x4 == g.L[3] - 1, wb = x4 == 0;
+        jn[6] = x1h + g.Lh * (wf ? r - (g.L[3] - 1) * st : r + st);
+        jn[7] = x1h + g.Lh * (wb ? r + (g.L[3] - 1) * st : r - st);
+        flip[6] = wf && g.bc[3] < 0;
+        flip[7] = wb && g.bc[3] < 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ju[k] = (k & 1) ? jn[k] : i;   // forward: U_mu(x); backward: U_mu(x - mu)
+}
 
 // FP64 needs more registers per thread than a 512-thread block allows.
 template <int P> struct HopMaxThreads { static constexpr int value = 512; };
@@ -256,42 +316,9 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     const int x1 = 2 * x1h + ((p + x2 + x3 + x4) & 1);
 
     const SpinorView in = sys_view<P>(hp.in, d);
-    // neighbour half-lattice index, link index and boundary flip of the 8 hops
-    int jn[8];
+    int jn[8], ju[8];
     bool flip[8];
-    {
-        const bool wf = x1 == g.L[0] - 1, wb = x1 == 0;
-        jn[0] = ((wf ? 0 : x1 + 1) >> 1) + g.Lh * r;
-        jn[1] = ((wb ? g.L[0] - 1 : x1 - 1) >> 1) + g.Lh * r;
-        flip[0] = wf && g.bc[0] < 0;
-        flip[1] = wb && g.bc[0] < 0;
-    }
-    {
-        const bool wf = x2 == g.L[1] - 1, wb = x2 == 0;
-        jn[2] = x1h + g.Lh * (wf ? r - (g.L[1] - 1) : r + 1);
-        jn[3] = x1h + g.Lh * (wb ? r + (g.L[1] - 1) : r - 1);
-        flip[2] = wf && g.bc[1] < 0;
-        flip[3] = wb && g.bc[1] < 0;
-    }
-    {
-        const int st = g.L[1];
-        const bool wf = x3 == g.L[2] - 1, wb = x3 == 0;
-        jn[4] = x1h + g.Lh * (wf ? r - (g.L[2] - 1) * st : r + st);
-        jn[5] = x1h + g.Lh * (wb ? r + (g.L[2] - 1) * st : r - st);
-        flip[4] = wf && g.bc[2] < 0;
-        flip[5] = wb && g.bc[2] < 0;
-    }
-    {
-        const int st = g.L[1] * g.L[2];
-        const bool wf = x4 == g.L[3] - 1, wb = x4 == 0;
-        jn[6] = x1h + g.Lh * (wf ? r - (g.L[3] - 1) * st : r + st);
-        jn[7] = x1h + g.Lh * (wb ? r + (g.L[3] - 1) * st : r - st);
-        flip[6] = wf && g.bc[3] < 0;
-        flip[7] = wb && g.bc[3] < 0;
-    }
-    int ju[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ju[k] = (k & 1) ? jn[k] : i;   // forward: U_mu(x); backward: U_mu(x - mu)
+    hop_neighbours(g, i, x1, x1h, r, x2, x3, x4, jn, ju, flip);
 
     cx<real> acc[12];
 #pragma unroll
@@ -342,6 +369,84 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
 }
 
+// R right-hand sides of one gauge field per thread: each link is loaded once
+// into registers and applied to the R half spinors (systems s0 .. s0+R-1 of a
+// uniform batch whose systems share the links).  hp.map counts groups of R.
+template <int P, bool DAG, int MODE, int R>
+__global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
+    using real = typename PT<P>::real;
+    int grp, tile;
+    map_block(hp.map, grp, tile);
+    const int s0 = grp * R;
+    if (hp.done) {
+        bool all = true;
+#pragma unroll
+        for (int r = 0; r < R; ++r) all = all && hp.done[(s0 + r) * hp.done_stride];
+        if (all) return;
+    }
+    const SysDesc& d0 = hp.sys[s0];
+    const Geom g = d0.g;
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    const int p = hp.parity, q = 1 - p;
+    const int x1h = i % g.Lh;
+    const int row = i / g.Lh;
+    const int x2 = row % g.L[1];
+    const int r2 = row / g.L[1];
+    const int x3 = r2 % g.L[2];
+    const int x4 = r2 / g.L[2];
+    const int x1 = 2 * x1h + ((p + x2 + x3 + x4) & 1);
+    int jn[8], ju[8];
+    bool flip[8];
+    hop_neighbours(g, i, x1, x1h, row, x2, x3, x4, jn, ju, flip);
+
+    cx<real> acc[R][12];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = mkc<real>(0, 0);
+    constexpr int SF = DAG ? +1 : -1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cx<real> u[9];
+        Access<P>::load_link(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cx<real> psi[12];
+            Access<P>::load_spinor(sys_view<P>(hp.in, hp.sys[s0 + r]), jn[k], psi);
+            hop_term_dec_d<SF>(k, acc[r], psi, u, flip[k]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const SysDesc& d = hp.sys[s0 + r];
+        const real a = (real)(hp.a_sign * d.kappa);
+        cx<real> v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = a * acc[r][k];
+        if (MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY || MODE == HOP_INV_XPAY) {
+            cx<real> y[12];
+            Access<P>::load_spinor(sys_view<P>(hp.y, d), i, y);
+            if (MODE == HOP_CLOV_XPAY) {
+                cx<real> ay[12];
+                clover_apply_site<P>(d.A[p], i, y, ay);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) v[k] = v[k] + ay[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) v[k] = v[k] + y[k];
+            }
+        }
+        if (MODE == HOP_INV || MODE == HOP_INV_XPAY) {
+            cx<real> w[12];
+            clover_apply_site<P>(d.Ainv[p], i, v, w);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = w[k];
+        }
+        Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
+    }
+}
+
 double hop_bytes_per_site(int prec, int mode) {
     const double S = spinor_bytes(prec), L = link_bytes(prec);
     const double C = (prec == P64 || prec == P64S) ? 576 : prec == P32 ? 288 : 144;
@@ -367,12 +472,61 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     hp.a_sign = a_sign;
     const std::string key = "hop" + std::to_string(P) + (DAG ? "d" : "n") + std::to_string(MODE) + "_" +
                             std::to_string(b.Vh_max) + "x" + std::to_string(b.nsys()) + (b.uniform ? "u" : "r");
+    const bool may_tune = out != y && out != in;
     auto run = [&](int B) {
         int nb = 0;
         hp.map = block_map(b, B, nb);
         k_hop<P, DAG, MODE><<<nb, B, 0, st>>>(hp);
     };
-    const int B = tuned_block(key, st, run, out != y && out != in, HopMaxThreads<P>::value);
+    // right-hand sides of one gauge field can share each link load in registers
+    bool shared = b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
+    for (int s = 1; shared && s < b.nsys(); ++s) shared = b.sys[s].U[0][0].data == b.sys[0].U[0][0].data;
+    auto run_multi = [&](int R, int B) {
+        BlockMap m;
+        m.nsys = b.nsys() / R;
+        m.uniform = 1;
+        m.tiles_per_sys = (b.Vh_max + B - 1) / B;
+        for (int t = 0; t <= MAXSYS; ++t) m.tile_start[t] = 0;
+        hp.map = m;
+        const int nb = m.tiles_per_sys * m.nsys;
+        if constexpr (P == P32 || P == P16) {
+            if (R == 2) k_hop_multi<P, DAG, MODE, 2><<<nb, B, 0, st>>>(hp);
+            else k_hop_multi<P, DAG, MODE, 4><<<nb, B, 0, st>>>(hp);
+        }
+    };
+    int R = 1;
+    if (shared) {
+        R = tune_lookup(key + "R");
+        if (R <= 0 && may_tune && !capturing(st)) {
+            // time the R = 1, 2, 4 variants (each with its own block size) and keep the fastest
+            cudaEvent_t e0, e1;
+            BPP_CUDA(cudaEventCreate(&e0));
+            BPP_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            R = 1;
+            for (int cand : {1, 2, 4}) {
+                if (b.nsys() % cand) continue;
+                int Bc;
+                if (cand == 1) Bc = tuned_block(key, st, run, true, HopMaxThreads<P>::value);
+                else Bc = tuned_block(key + "R" + std::to_string(cand), st, [&](int B) { run_multi(cand, B); }, true, 256);
+                auto go = [&]() { if (cand == 1) run(Bc); else run_multi(cand, Bc); };
+                go();
+                BPP_CUDA(cudaEventRecord(e0, st));
+                for (int rep = 0; rep < 3; ++rep) go();
+                BPP_CUDA(cudaEventRecord(e1, st));
+                BPP_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BPP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; R = cand; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            tune_store(key + "R", R);
+        }
+        if (R <= 0) R = 1;
+    }
+    const int B = R == 1 ? tuned_block(key, st, run, may_tune, HopMaxThreads<P>::value)
+                         : tuned_block(key + "R" + std::to_string(R), st, [&](int Bx) { run_multi(R, Bx); }, may_tune, 256);
     // algorithmic bytes: systems that share a gauge field (the right-hand sides
     // of one lattice) read its links once per launch
     double sites = 0, bytes = 0;
@@ -387,7 +541,8 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
         bytes += per_sys[s];
     }
     ProfScope prof(P, bytes, st);
-    run(B);
+    if (R == 1) run(B);
+    else run_multi(R, B);
     count_launch();
     BPP_CHECK_LAUNCH();
     if (thread_capturing()) {

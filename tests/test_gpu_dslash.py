@@ -113,3 +113,25 @@ def test_dslash_f64df(L, parity):
     print(f"double-float dslash norm-relative error {err:.2e}")
     assert err <= 1e-12
     assert max_err(out, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("nrhs", [2, 4, 6, 12])
+def test_dslash_multi_rhs_low_precision(prec, nrhs):
+    """Right-hand sides of one gauge field (the register-blocked path shares each
+    link load): every RHS matches its own single-RHS result and the oracle."""
+    bpp = lib()
+    L = (8, 8, 8, 8)
+    g, U = gauge(L)
+    Vh = oracle.volume(L) // 2
+    psis = synth.gaussian_spinor(L, seed=5, nrhs=nrhs)[:, :Vh]
+    if prec == 1:
+        psis = round32(psis)
+    dev = to_dev(psis, torch.complex64)
+    for parity in (0, 1):
+        out = to_np(bpp.dslash(g, dev, KAPPA, parity, prec))
+        for r in range(nrhs):
+            one = to_np(bpp.dslash(g, dev[r].contiguous(), KAPPA, parity, prec))
+            assert rel_err(out[r], one) <= (1e-6 if prec == 1 else 5e-3)
+        ref = oracle.hop_eo(round32(U) if prec == 1 else U, psis[nrhs - 1], KAPPA, L, parity, BC)
+        assert rel_err(out[nrhs - 1], ref) <= (1e-6 if prec == 1 else 5e-3)
