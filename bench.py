@@ -239,7 +239,7 @@ def run_ours(args, rank, world):
     del U
     b = torch.from_numpy(b_np).to(dev)
     x = torch.empty_like(b)
-    opts = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=not args.eager)
+    opts = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0 if args.eager else 2)
     stream = torch.cuda.current_stream()
 
     # warm-up (also runs the block-size autotuner on first use)
@@ -281,7 +281,7 @@ def run_ours(args, rank, world):
     bpp.prof_enable(True)
     for p in (0, 1, 2, 3):
         bpp.prof_read(p, reset=True)
-    bpp.solve(g, b, KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=False), x=x)
+    bpp.solve(g, b, KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0), x=x)
     torch.cuda.synchronize()
     bpp.prof_enable(False)
     prof = {p: bpp.prof_read(p, reset=True) for p in (0, 1, 2, 3)}
@@ -342,7 +342,7 @@ def run_ours(args, rank, world):
         fp64_ms = e0.elapsed_time(e1)
     native_outer_ms = None
     if not args.no_fp64:
-        on = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=not args.eager, outer_df64=False)
+        on = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0 if args.eager else 2, outer_df64=False)
         bpp.solve(g, b, KAPPA, 0.0, TOL, on, x=x)
         torch.cuda.synchronize()
         e0.record(stream)

@@ -179,9 +179,15 @@ typedef struct {
     int use_x0;       /* nonzero: x holds the initial guess on entry */
     int dagger;       /* nonzero: solve D^dag x = b (through gamma5-hermiticity) */
     int check_every;  /* inner iterations between host-side convergence checks (eager mode) */
-    int use_graph;    /* nonzero: run each inner solve as one CUDA graph launch whose
-                         conditional while node repeats one Krylov iteration until every
-                         system has converged (no host round trip per iteration) */
+    int use_graph;    /* 0: host-driven loops; 1: each inner solve is one CUDA graph
+                         launch whose conditional while node repeats one Krylov iteration
+                         until every system has converged; 2: the whole correction loop
+                         (outer decisions by device control kernels, inner solves,
+                         defect updates, true-residual checks) is one graph launch with
+                         nested conditional nodes.  With 2 the first solve of a
+                         configuration runs host-driven (autotuning) and captures the
+                         graph; later solves replay it.  All modes compute identical
+                         results. */
     int outer_arith;  /* 0: every outer-loop operator application in FP64 arithmetic;
                          1: the even-odd preparation and the intermediate defects
                          bhat - Mhat x in double-float arithmetic (FP64 values held as
@@ -201,7 +207,7 @@ typedef struct {
 } bpp_solve_stats;
 
 /* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 0 (per precision),
- * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 1,
+ * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 2,
  * outer_arith 1. */
 void bpp_solve_opts_default(bpp_solve_opts* opts);
 

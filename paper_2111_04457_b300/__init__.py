@@ -280,10 +280,12 @@ def dirac_apply(g: Gauge, x: torch.Tensor, kappa: float, csw: float = 0.0, dagge
 
 
 def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000, max_outer=50, dagger=False,
-               check_every=4, use_x0=False, use_graph=True, outer_df64=True) -> SolveOpts:
-    """Solver options (bpp_solve_opts).  outer_df64: intermediate defects of the
-    FP64 outer loop in double-float arithmetic (the final true residual, the
-    solution accumulation and the norms stay FP64)."""
+               check_every=4, use_x0=False, use_graph=2, outer_df64=True) -> SolveOpts:
+    """Solver options (bpp_solve_opts).  use_graph: 0 host-driven, 1 inner loop as
+    a CUDA graph, 2 whole correction loop as one graph launch (default).
+    outer_df64: intermediate defects of the FP64 outer loop in double-float
+    arithmetic (the final true residual, the solution accumulation and the
+    norms stay FP64)."""
     o = SolveOpts()
     _lib.bpp_solve_opts_default(ctypes.byref(o))
     o.solver = solver

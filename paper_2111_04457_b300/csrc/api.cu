@@ -254,7 +254,7 @@ void bpp_solve_opts_default(bpp_solve_opts* o) {
     o->use_x0 = 0;
     o->dagger = 0;
     o->check_every = 4;
-    o->use_graph = 1;
+    o->use_graph = 2;
     o->outer_arith = 1;
 }
 

@@ -386,8 +386,8 @@ bool thread_capturing();
 void add_hop_work(int prec, int64_t launches, double bytes);
 void capture_hop_work(int prec, int sys, double bytes);
 void capture_work_reset(int nsys);
-const std::vector<double>& capture_work_bytes();
-int capture_work_prec();
+const std::vector<double>& capture_work_bytes(int prec);
+int64_t capture_launches();
 // True while `s` is being captured into a CUDA graph.
 bool capturing(cudaStream_t s);
 // Chooses the block size for a launch identified by `key` (kernel + shape).
@@ -428,11 +428,11 @@ struct DevBuf {
 
 template <class Run>
 int tuned_block(const std::string& key, cudaStream_t s, Run run, bool may_tune = true, int max_block = 512,
-                int min_block = 64) {
+                int min_block = 32) {
     int b = tune_lookup(key);
     if (b > 0) return b;
     if (!may_tune || capturing(s)) return max_block < 256 ? max_block : 256;
-    static const int cand_all[] = {64, 128, 256, 512};
+    static const int cand_all[] = {32, 64, 128, 256, 512};
     std::vector<int> cand;
     for (int c : cand_all)
         if (c <= max_block && c >= min_block) cand.push_back(c);

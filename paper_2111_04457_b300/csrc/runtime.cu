@@ -22,8 +22,8 @@ bool thread_capturing() { return t_capturing; }
 static std::mutex g_work_mu;
 static int64_t g_work_n[NPREC] = {};
 static double g_work_bytes[NPREC] = {};
-static thread_local std::vector<double> t_cap_bytes;
-static thread_local int t_cap_prec = 0;
+static thread_local std::vector<double> t_cap_bytes[NPREC];
+static thread_local int64_t t_cap_launches = 0;
 
 void add_hop_work(int prec, int64_t launches, double bytes) {
     std::lock_guard<std::mutex> lk(g_work_mu);
@@ -31,13 +31,15 @@ void add_hop_work(int prec, int64_t launches, double bytes) {
     g_work_bytes[prec] += bytes;
 }
 void capture_hop_work(int prec, int sys, double bytes) {
-    if ((int)t_cap_bytes.size() <= sys) t_cap_bytes.resize(sys + 1, 0.0);
-    t_cap_bytes[sys] += bytes;
-    t_cap_prec = prec;
+    if ((int)t_cap_bytes[prec].size() <= sys) t_cap_bytes[prec].resize(sys + 1, 0.0);
+    t_cap_bytes[prec][sys] += bytes;
 }
-void capture_work_reset(int nsys) { t_cap_bytes.assign(nsys, 0.0); }
-const std::vector<double>& capture_work_bytes() { return t_cap_bytes; }
-int capture_work_prec() { return t_cap_prec; }
+void capture_work_reset(int nsys) {
+    for (auto& v : t_cap_bytes) v.assign(nsys, 0.0);
+    t_cap_launches = 0;
+}
+const std::vector<double>& capture_work_bytes(int prec) { return t_cap_bytes[prec]; }
+int64_t capture_launches() { return t_cap_launches; }
 
 int work_read(int prec, int64_t* n, double* bytes, int reset) {
     if (prec < 0 || prec >= NPREC) return BPP_ERR_INVALID_ARG;
@@ -50,6 +52,7 @@ int work_read(int prec, int64_t* n, double* bytes, int reset) {
 
 void count_launch(int64_t n) {
     if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+    else t_cap_launches += n;
 }
 
 bool capturing(cudaStream_t s) {

@@ -24,6 +24,7 @@
 
 #include "blas.h"
 #include "kernels.h"
+#include "outer.h"
 #include "solver.h"
 
 namespace bpp {
@@ -50,13 +51,21 @@ static void write_scalars(DevBuf& d, const std::vector<KScal>& h, cudaStream_t s
 
 // Loop control of the graph-captured inner solve: keep iterating while any
 // system is active, at most max_loops times.
+// Sets a graph condition.  A handle's default value is applied when the
+// top-level graph is launched, not each time an enclosing body runs again, so
+// a nested while loop is re-armed explicitly before it is reached.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned v) { cudaGraphSetConditional(h, v); }
+
+// loops[0] counts the passes of this inner solve, loops[1] all passes since
+// the solve started.
 __global__ void k_loop_ctl(const KScal* sc, int n, int* loops, int max_loops, cudaGraphConditionalHandle h) {
     bool active = false;
     for (int s = threadIdx.x; s < n; s += 32) active = active || !sc[s].done;
     active = __any_sync(0xffffffffu, active);
     if (threadIdx.x == 0) {
-        const int l = *loops + 1;
-        *loops = l;
+        const int l = loops[0] + 1;
+        loops[0] = l;
+        loops[1] += 1;
         cudaGraphSetConditional(h, (active && l < max_loops) ? 1u : 0u);
     }
 }
@@ -77,7 +86,7 @@ struct Plan {
     Vec be_s, bo_s, bhat_s, xe_s, m_s, tmpo_s, r_s;
     Vec w[9];
     RedBuf rb;
-    DevBuf d64, dP, dloops;
+    DevBuf d64, dP, dloops, dod, doc;
     std::vector<KScal> h64, hP;
     bool warmed = false;                 // one eager inner solve ran (autotuner populated)
     cudaGraph_t graph = nullptr;
@@ -85,11 +94,22 @@ struct Plan {
     int graph_max_iter = -1;
     int body_kernels = 0;
     std::vector<double> iter_bytes;      // hopping-kernel bytes of one iteration, per system
+    // the whole solve (outer loop included) as one graph launch
+    cudaGraph_t wgraph = nullptr;
+    cudaGraphExec_t wexec = nullptr;
+    int wgraph_max_iter = -1;
+    bool whole_warm = false;             // one host-driven solve ran (every branch kernel tuned)
+    std::vector<double> w_iter_bytes;    // per system, inner precision
+    double w_full_bytes[NPREC] = {}, w_rel_bytes[NPREC] = {}, w_schur_bytes[NPREC] = {};
+    int64_t w_full_launch = 0, w_rel_launch = 0, w_schur_launch = 0, w_iter_launch = 0;
+    int64_t w_inner_launch = 0, w_pass_launch = 0;
     size_t bytes = 0;
     uint64_t last_use = 0;
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (wexec) cudaGraphExecDestroy(wexec);
+        if (wgraph) cudaGraphDestroy(wgraph);
     }
 };
 
@@ -159,7 +179,9 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     pl->rb.persistent = true;
     pl->d64.alloc_persistent(n * sizeof(KScal));
     pl->dP.alloc_persistent(n * sizeof(KScal));
-    pl->dloops.alloc_persistent(sizeof(int));
+    pl->dloops.alloc_persistent(2 * sizeof(int));
+    pl->dod.alloc_persistent(n * sizeof(OuterDev));
+    pl->doc.alloc_persistent(sizeof(OuterCtl));
     BPP_CUDA(cudaMemset(pl->d64.p, 0, n * sizeof(KScal)));
     BPP_CUDA(cudaMemset(pl->dP.p, 0, n * sizeof(KScal)));
     pl->h64.resize(n);
@@ -275,7 +297,7 @@ static void build_graph(Plan& pl, int max_iter) {
             throw;
         }
         set_capturing(false);
-        pl.iter_bytes = capture_work_bytes();
+        pl.iter_bytes = capture_work_bytes(pl.prec);
         cudaGraph_t captured;
         BPP_CUDA(cudaStreamEndCapture(cs, &captured));
         BPP_CUDA(cudaGraphInstantiate(&pl.exec, pl.graph, 0));
@@ -295,7 +317,7 @@ static void inner_solve(Plan& pl, const bpp_solve_opts& o, cudaStream_t st) {
     inner_init(pl, v, tmp, st);
     if (o.use_graph && pl.warmed) {
         if (!pl.exec || pl.graph_max_iter != o.max_inner) build_graph(pl, o.max_inner);
-        BPP_CUDA(cudaMemsetAsync(pl.dloops.p, 0, sizeof(int), st));
+        BPP_CUDA(cudaMemsetAsync(pl.dloops.p, 0, sizeof(int), st));   // this solve's pass counter
         BPP_CUDA(cudaGraphLaunch(pl.exec, st));
         int loops = 0;
         BPP_CUDA(cudaMemcpyAsync(&loops, pl.dloops.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -317,6 +339,79 @@ static void inner_solve(Plan& pl, const bpp_solve_opts& o, cudaStream_t st) {
         if (all) break;
     }
     pl.warmed = true;
+}
+
+// ----------------------------------------------------------------------------- capture helpers
+// Graph currently captured on stream cs.
+static cudaGraph_t capture_graph(cudaStream_t cs) {
+    cudaStreamCaptureStatus stt;
+    cudaGraph_t g = nullptr;
+    BPP_CUDA(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, nullptr, nullptr, nullptr));
+    BPP_REQUIRE(stt == cudaStreamCaptureStatusActive && g, BPP_ERR_CUDA, "stream is not capturing");
+    return g;
+}
+
+static unsigned long long new_handle(cudaStream_t cs, unsigned dflt) {
+    cudaGraphConditionalHandle h;
+    BPP_CUDA(cudaGraphConditionalHandleCreate(&h, capture_graph(cs), dflt, cudaGraphCondAssignDefault));
+    return (unsigned long long)h;
+}
+
+// Appends a conditional node after everything captured so far on cs and
+// returns its body graphs.
+static std::vector<cudaGraph_t> add_conditional(cudaStream_t cs, unsigned long long h, cudaGraphConditionalNodeType type,
+                                                unsigned size) {
+    cudaStreamCaptureStatus stt;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    BPP_CUDA(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, &deps, &edata, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = (cudaGraphConditionalHandle)h;
+    cp.conditional.type = type;
+    cp.conditional.size = size;
+    cudaGraphNode_t node;
+    BPP_CUDA(cudaGraphAddNode(&node, g, deps, edata, nd, &cp));
+    BPP_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    std::vector<cudaGraph_t> bodies(cp.conditional.phGraph_out, cp.conditional.phGraph_out + size);
+    return bodies;
+}
+
+// Captures f(stream) into the (empty) body graph.
+template <class F>
+static void capture_body(cudaGraph_t body, F f) {
+    cudaStream_t cs;
+    BPP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    BPP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        f(cs);
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cs, &dummy);
+        cudaStreamDestroy(cs);
+        throw;
+    }
+    cudaGraph_t captured;
+    const cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    BPP_CUDA(e);
+}
+
+struct CapSnap {
+    double bytes[NPREC];
+    int64_t launches;
+};
+static CapSnap cap_snap(int n) {
+    CapSnap c;
+    for (int p = 0; p < NPREC; ++p) {
+        c.bytes[p] = 0.0;
+        const auto& v = capture_work_bytes(p);
+        for (int s = 0; s < n && s < (int)v.size(); ++s) c.bytes[p] += v[s];
+    }
+    c.launches = capture_launches();
+    return c;
 }
 
 int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& kappa, bool clover,
@@ -403,61 +498,65 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         if (split) BPP_CUDA(cudaMemsetAsync(pl.xe_s.p(), 0, b64s.vec_bytes, st));
     }
 
-    // Outer loop.  r holds the even defect; after a "full" residual it is the
-    // even part of b - D x (equal to bhat - Mhat x_e, since x_o is
-    // reconstructed from x_e) and rr_o the odd part, so the full FP64 true
-    // residual is known.  A correction predicted to reach the target is
-    // followed directly by the full residual (3 hopping launches) instead of the
-    // Schur residual (2) plus a separate check (3).
-    std::vector<double> target(n, tol), rr_e(n, 0.0), rr_o(n, 0.0), pred(n, 0.0);
-    std::vector<int> outer(n, 0), inner_it(n, 0), conv(n, 0), status(n, BPP_OK);
-    std::vector<double> true_res(n, 0.0);
-    bool have_full = false;
-    bool defect_split = false;   // the current defect lives in r_s (split) rather than r (FP64)
-    // Accumulated error of FP32 recursive defect updates since the last
-    // recomputation, estimated as 4 * 2^-24 * ||Mhat e|| * scale per update.
-    std::vector<double> drift(n, 0.0);
-    const double eps32 = 4.0 * 5.96e-8;
-    auto read_rr = [&](std::vector<double>& dst) {
-        read_scalars(pl.d64, h64, st);
-        for (int s = 0; s < n; ++s) dst[s] = h64[s].rr;
-    };
-    auto schur_residual = [&]() {
-        std::fill(drift.begin(), drift.end(), 0.0);
-        if (split) {
-            schur(b64s, clover, dag, pl.xe_s.p(), pl.m_s.p(), pl.tmpo_s.p(), st);
-            split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r_s.p(), sc64, pl.rb, st);
-            defect_split = true;
-        } else {
-            schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
-            outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
-        }
-        read_rr(rr_e);
-        have_full = false;
-    };
-    auto full_residual = [&]() {
+    // Outer loop.  r (FP64) or r_s (split) holds the even defect; after a
+    // "full" residual it is the even part of b - D x (equal to bhat - Mhat x_e,
+    // since x_o is reconstructed from x_e) and rr_o the odd part, so the full
+    // FP64 true residual is known.  The decisions are taken by the control
+    // kernels of outer.cu on device state (OuterDev / OuterCtl): the host-driven
+    // loop reads their flags back and launches the chosen branch; the
+    // whole-solve graph branches on the same flags with conditional nodes.
+    OuterDev* od = pl.dod.as<OuterDev>();
+    OuterCtl* oc = pl.doc.as<OuterCtl>();
+    KScal* scP = pl.dP.as<KScal>();
+    const double eps32 = 4.0 * 5.96e-8;   // per-update error bound of a reliable FP32 defect update
+    std::vector<OuterDev> hod(n);
+    OuterCtl hoc{};
+
+    // the branch kernel sequences (host-driven and captured alike)
+    auto full_kernels = [&](cudaStream_t cs) {
         // x_o = A_oo^-1 (b_o + kappa H_oe x_e) (double-float when split, then its
         // exact FP64 value); De = A_ee x_e - kappa H_eo x_o; Do = A_oo x_o - kappa H_oe x_e
         // in FP64: the true residual of the returned x
         if (split) {
-            hop(b64s, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe_s.p(), pl.tmpo_s.p(), pl.bo_s.p(), st);
-            split_to_f64(b64, pl.tmpo_s.p(), pl.xo.p(), st);
+            hop(b64s, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe_s.p(), pl.tmpo_s.p(), pl.bo_s.p(), cs);
+            split_to_f64(b64, pl.tmpo_s.p(), pl.xo.p(), cs);
         } else {
-            hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), st);
+            hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), cs);
         }
-        hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xo.p(), pl.r.p(), pl.xe.p(), st);
-        outer_residual(b64, pl.be.p(), pl.r.p(), sc64, pl.rb, st);
-        read_rr(rr_e);
-        hop(b64, 1, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xe.p(), pl.tmpo.p(), pl.xo.p(), st);
-        outer_residual(b64, pl.bo.p(), pl.tmpo.p(), sc64, pl.rb, st);
-        read_rr(rr_o);
-        have_full = true;
-        defect_split = false;
-        // outer_residual left the odd norm in the scalars; restore the even one
-        // for the downcast of the next correction
-        for (int s = 0; s < n; ++s) { h64[s].rr = rr_e[s]; h64[s].scale = std::sqrt(std::max(rr_e[s], 0.0)); }
-        write_scalars(pl.d64, h64, st);
+        hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xo.p(), pl.r.p(), pl.xe.p(), cs);
+        outer_residual(b64, pl.be.p(), pl.r.p(), sc64, pl.rb, cs);
+        oc_full_even(od, sc64, n, cs);
+        hop(b64, 1, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xe.p(), pl.tmpo.p(), pl.xo.p(), cs);
+        outer_residual(b64, pl.bo.p(), pl.tmpo.p(), sc64, pl.rb, cs);
+        oc_full_odd(od, oc, sc64, cs);
     };
+    auto reliable_kernels = [&](cudaStream_t cs) {
+        to_f32(bP, pl.b32, pl.w[1].p(), pl.e32.p(), cs);
+        schur(pl.b32, clover, dag, pl.e32.p(), pl.m32.p(), pl.tmp32.p(), cs);
+        defect_update(b64, pl.b32, pl.r_s.p(), pl.m32.p(), sc64, pl.rb, cs);
+        oc_after_reliable(od, oc, sc64, cs);
+    };
+    auto schur_kernels = [&](cudaStream_t cs) {
+        if (split) {
+            schur(b64s, clover, dag, pl.xe_s.p(), pl.m_s.p(), pl.tmpo_s.p(), cs);
+            split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r_s.p(), sc64, pl.rb, cs);
+        } else {
+            schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), cs);
+            outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, cs);
+        }
+        oc_after_schur(od, oc, sc64, cs);
+    };
+    auto downcast = [&](bool from_split, cudaStream_t cs) {
+        outer_downcast(b64, bP, from_split ? pl.r_s.p() : pl.r.p(), pl.w[0].p(), sc64, cs, from_split);
+    };
+    auto read_state = [&]() {
+        BPP_CUDA(cudaMemcpyAsync(hod.data(), od, n * sizeof(OuterDev), cudaMemcpyDeviceToHost, st));
+        BPP_CUDA(cudaMemcpyAsync(&hoc, oc, sizeof(OuterCtl), cudaMemcpyDeviceToHost, st));
+        BPP_CUDA(cudaStreamSynchronize(st));
+    };
+
+    // initial defect
+    bool defect_split = false;
     if (x_zero) {
         if (split) {
             split_residual(b64, pl.bhat_s.p(), nullptr, pl.r_s.p(), sc64, pl.rb, st);
@@ -466,87 +565,191 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
             BPP_CUDA(cudaMemsetAsync(pl.r.p(), 0, b64.vec_bytes, st));
             outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
         }
-        read_rr(rr_e);
+    } else if (split) {
+        schur(b64s, clover, dag, pl.xe_s.p(), pl.m_s.p(), pl.tmpo_s.p(), st);
+        split_residual(b64, pl.bhat_s.p(), pl.m_s.p(), pl.r_s.p(), sc64, pl.rb, st);
+        defect_split = true;
     } else {
-        schur_residual();
+        schur(b64, clover, dag, pl.xe.p(), pl.r.p(), pl.tmpo.p(), st);
+        outer_residual(b64, pl.bhat.p(), pl.r.p(), sc64, pl.rb, st);
     }
-    const int max_passes = o.max_outer + 8;
-    for (int pass = 0; pass < max_passes; ++pass) {
-        bool need_check = false, any_active = false;
-        std::vector<int> active(n, 0);
-        for (int s = 0; s < n; ++s) {
-            if (status[s] != BPP_OK || conv[s]) continue;
-            const double rr = rr_e[s] + (have_full ? rr_o[s] : 0.0);
-            if (!std::isfinite(rr)) { status[s] = BPP_ERR_NONFINITE; continue; }
-            const double rel = bnorm2[s] > 0.0 ? std::sqrt(rr / bnorm2[s]) : 0.0;
-            if (bnorm2[s] == 0.0) { conv[s] = 1; true_res[s] = 0.0; continue; }
-            if (have_full) {
-                true_res[s] = rel;
-                if (rel <= tol) { conv[s] = 1; continue; }
-                if (rel <= target[s]) target[s] *= 0.5 * tol / rel;    // Schur target met but not the true one
-            } else if (rel <= target[s]) {
-                need_check = true;                                      // confirm with the full residual
-                continue;
+    read_scalars(pl.d64, h64, st);
+    for (int s = 0; s < n; ++s) {
+        OuterDev d{};
+        d.rr_e = h64[s].rr;
+        d.target = tol;
+        d.bnorm2 = bnorm2[s];
+        d.status = BPP_OK;
+        hod[s] = d;
+    }
+    hoc.tol = tol;
+    hoc.inner_tol = o.inner_tol;
+    hoc.eps32 = eps32;
+    hoc.n = n;
+    hoc.max_outer = o.max_outer;
+    hoc.max_passes = o.max_outer + 8;
+    hoc.max_inner = o.max_inner;
+    hoc.prec = bP.prec;
+    hoc.split = split;
+    hoc.reliable = pl.reliable;
+    hoc.defect_split = defect_split;
+    BPP_CUDA(cudaMemcpyAsync(od, hod.data(), n * sizeof(OuterDev), cudaMemcpyHostToDevice, st));
+    BPP_CUDA(cudaMemcpyAsync(oc, &hoc, sizeof(OuterCtl), cudaMemcpyHostToDevice, st));
+
+    if (o.use_graph == 2 && pl.whole_warm) {
+        // the whole correction loop as one graph launch
+        if (!pl.wexec || pl.wgraph_max_iter != o.max_inner) {
+            if (pl.wexec) { cudaGraphExecDestroy(pl.wexec); pl.wexec = nullptr; }
+            if (pl.wgraph) { cudaGraphDestroy(pl.wgraph); pl.wgraph = nullptr; }
+            BPP_CUDA(cudaStreamSynchronize(st));
+            cudaStream_t s0;
+            BPP_CUDA(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+            BPP_CUDA(cudaGraphCreate(&pl.wgraph, 0));
+            capture_work_reset(n);
+            set_capturing(true);
+            try {
+                BPP_CUDA(cudaStreamBeginCaptureToGraph(s0, pl.wgraph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+                const unsigned long long h_outer = new_handle(s0, 1);
+                auto outer_body = add_conditional(s0, h_outer, cudaGraphCondTypeWhile, 1);
+                capture_body(outer_body[0], [&](cudaStream_t s1) {
+                    const unsigned long long h_check = new_handle(s1, 0), h_inner = new_handle(s1, 0);
+                    const CapSnap p0 = cap_snap(n);
+                    oc_classify(od, oc, h_check, h_inner, s1);
+                    const CapSnap p1 = cap_snap(n);
+                    capture_body(add_conditional(s1, h_check, cudaGraphCondTypeIf, 1)[0], full_kernels);
+                    const CapSnap p2 = cap_snap(n);
+                    for (int q = 0; q < NPREC; ++q) pl.w_full_bytes[q] = p2.bytes[q] - p1.bytes[q];
+                    pl.w_full_launch = p2.launches - p1.launches;
+                    capture_body(add_conditional(s1, h_inner, cudaGraphCondTypeIf, 1)[0], [&](cudaStream_t s2) {
+                        const unsigned long long h_split = new_handle(s2, 0), h_branch = new_handle(s2, 0);
+                        const CapSnap i0 = cap_snap(n);
+                        oc_inner_setup(od, oc, sc64, scP, h_split, s2);
+                        auto dc = add_conditional(s2, h_split, cudaGraphCondTypeIf, 2);
+                        capture_body(dc[0], [&](cudaStream_t s3) { downcast(true, s3); });
+                        capture_body(dc[1], [&](cudaStream_t s3) { downcast(false, s3); });
+                        BlasVecs v = inner_vecs(pl);
+                        inner_init(pl, v, pl.w[8].p(), s2);
+                        BPP_CUDA(cudaMemsetAsync(pl.dloops.p, 0, sizeof(int), s2));
+                        const unsigned long long h_it = new_handle(s2, 1);
+                        k_set_cond<<<1, 1, 0, s2>>>((cudaGraphConditionalHandle)h_it, 1u);
+                        count_launch();
+                        BPP_CHECK_LAUNCH();
+                        const CapSnap i1 = cap_snap(n);
+                        const std::vector<double> before = capture_work_bytes(bP.prec);
+                        capture_body(add_conditional(s2, h_it, cudaGraphCondTypeWhile, 1)[0], [&](cudaStream_t s3) {
+                            inner_iteration(pl, v, pl.w[8].p(), s3);
+                            k_loop_ctl<<<1, 32, 0, s3>>>(scP, n, pl.dloops.as<int>(), o.max_inner + 1,
+                                                         (cudaGraphConditionalHandle)h_it);
+                            count_launch();
+                            BPP_CHECK_LAUNCH();
+                        });
+                        const CapSnap i2 = cap_snap(n);
+                        pl.w_iter_bytes.assign(n, 0.0);
+                        {
+                            const auto& after = capture_work_bytes(bP.prec);
+                            for (int s = 0; s < n; ++s)
+                                pl.w_iter_bytes[s] = (s < (int)after.size() ? after[s] : 0.0) -
+                                                     (s < (int)before.size() ? before[s] : 0.0);
+                        }
+                        pl.w_iter_launch = i2.launches - i1.launches;
+                        outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, s2, split ? pl.xe_s.p() : nullptr);
+                        oc_decide(od, oc, scP, h_branch, s2);
+                        const CapSnap i3 = cap_snap(n);
+                        // both downcast variants were captured, one runs
+                        pl.w_inner_launch = (i1.launches - i0.launches) - 1 + (i3.launches - i2.launches);
+                        auto br = add_conditional(s2, h_branch, cudaGraphCondTypeSwitch, 3);
+                        const CapSnap b0 = cap_snap(n);
+                        capture_body(br[OB_FULL], full_kernels);
+                        const CapSnap b1 = cap_snap(n);
+                        if (pl.reliable) capture_body(br[OB_RELIABLE], reliable_kernels);
+                        const CapSnap b2 = cap_snap(n);
+                        capture_body(br[OB_SCHUR], schur_kernels);
+                        const CapSnap b3 = cap_snap(n);
+                        for (int q = 0; q < NPREC; ++q) {
+                            pl.w_rel_bytes[q] = b2.bytes[q] - b1.bytes[q];
+                            pl.w_schur_bytes[q] = b3.bytes[q] - b2.bytes[q];
+                        }
+                        pl.w_rel_launch = b2.launches - b1.launches;
+                        pl.w_schur_launch = b3.launches - b2.launches;
+                    });
+                    oc_loop(oc, h_outer, s1);
+                    pl.w_pass_launch = 2;
+                    (void)p0;
+                });
+                cudaGraph_t captured;
+                BPP_CUDA(cudaStreamEndCapture(s0, &captured));
+            } catch (...) {
+                set_capturing(false);
+                cudaGraph_t dummy;
+                cudaStreamEndCapture(s0, &dummy);
+                cudaStreamDestroy(s0);
+                if (pl.wgraph) { cudaGraphDestroy(pl.wgraph); pl.wgraph = nullptr; }
+                throw;
             }
-            if (outer[s] >= o.max_outer) continue;
-            active[s] = 1;
-            any_active = true;
+            set_capturing(false);
+            cudaStreamDestroy(s0);
+            BPP_CUDA(cudaGraphInstantiate(&pl.wexec, pl.wgraph, 0));
+            pl.wgraph_max_iter = o.max_inner;
         }
-        if (need_check && !have_full) { full_residual(); continue; }
-        if (!any_active) break;
-        // inner solve of Mhat e = r/||r|| for the active systems
-        for (int s = 0; s < n; ++s) {
-            h64[s].rr = rr_e[s];
-            h64[s].scale = active[s] ? std::sqrt(std::max(rr_e[s], 0.0)) : 0.0;
-            KScal k{};
-            const double rn = std::sqrt(std::max(rr_e[s], 0.0));
-            const double need = 0.5 * target[s] * std::sqrt(bnorm2[s]) / std::max(rn, 1e-300);
-            // inner_tol <= 0: per-precision default (FP32 1e-6, FP16 2e-3)
-            const double dflt = bP.prec == P32 ? 1e-6 : 2e-3;
-            const double want = o.inner_tol > 0.0 ? o.inner_tol : dflt;
-            const double itol = bP.prec == P64 ? need : std::max(want, need);
-            k.tol2 = itol * itol;
-            k.max_iter = o.max_inner;
-            hP[s] = k;
+        BPP_CUDA(cudaMemsetAsync(pl.dloops.p, 0, 2 * sizeof(int), st));
+        BPP_CUDA(cudaGraphLaunch(pl.wexec, st));
+        read_state();
+        int loops[2] = {0, 0};
+        BPP_CUDA(cudaMemcpy(loops, pl.dloops.p, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+        // credit the work the graph did: every inner iteration of an active
+        // system, and every executed branch for all systems
+        for (int q = 0; q < NPREC; ++q) {
+            double by = hoc.n_full * pl.w_full_bytes[q] + hoc.n_rel * pl.w_rel_bytes[q] + hoc.n_schur * pl.w_schur_bytes[q];
+            if (q == bP.prec)
+                for (int s = 0; s < n; ++s) by += hod[s].inner_it * pl.w_iter_bytes[s];
+            if (by > 0) add_hop_work(q, 0, by);
         }
-        write_scalars(pl.d64, h64, st);
-        write_scalars(pl.dP, hP, st);
-        outer_downcast(b64, bP, defect_split ? pl.r_s.p() : pl.r.p(), pl.w[0].p(), sc64, st, defect_split);
-        inner_solve(pl, o, st);
-        outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st, split ? pl.xe_s.p() : nullptr);
-        bool all_predicted = true;
-        for (int s = 0; s < n; ++s) {
-            if (!active[s]) continue;
-            outer[s] += 1;
-            inner_it[s] += hP[s].iter;
-            const double inner_rel = hP[s].bb > 0.0 ? std::sqrt(std::max(hP[s].rr, 0.0) / hP[s].bb) : 0.0;
-            pred[s] = std::sqrt(std::max(rr_e[s], 0.0)) * inner_rel;
-            if (!(pred[s] <= 0.5 * target[s] * std::sqrt(bnorm2[s]))) all_predicted = false;
+        count_launch((int64_t)hoc.passes * pl.w_pass_launch + (int64_t)hoc.n_inner * pl.w_inner_launch +
+                     (int64_t)loops[1] * pl.w_iter_launch + (int64_t)hoc.n_full * pl.w_full_launch +
+                     (int64_t)hoc.n_rel * pl.w_rel_launch + (int64_t)hoc.n_schur * pl.w_schur_launch);
+    } else {
+        for (int pass = 0; pass < hoc.max_passes; ++pass) {
+            oc_classify(od, oc, 0, 0, st);
+            read_state();
+            if (hoc.check) {
+                full_kernels(st);
+            } else if (hoc.inner) {
+                oc_inner_setup(od, oc, sc64, scP, 0, st);
+                downcast(hoc.defect_split != 0, st);
+                inner_solve(pl, o, st);
+                outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st, split ? pl.xe_s.p() : nullptr);
+                oc_decide(od, oc, scP, 0, st);
+                read_state();
+                if (hoc.branch == OB_FULL) full_kernels(st);
+                else if (hoc.branch == OB_RELIABLE) reliable_kernels(st);
+                else schur_kernels(st);
+            }
+            oc_loop(oc, 0, st);
+            if (!hoc.check && !hoc.inner) break;
         }
-        // recursive FP32 update of the defect when its accumulated error stays
-        // below 1% of the defect it predicts; otherwise recompute it
-        bool reliable_ok = pl.reliable && defect_split;
-        for (int s = 0; s < n; ++s) {
-            if (!active[s]) continue;
-            const double step = eps32 * std::sqrt(std::max(rr_e[s], 0.0));
-            if (!(drift[s] + step <= 0.01 * pred[s])) reliable_ok = false;
-        }
-        if (all_predicted) {
-            full_residual();
-        } else if (reliable_ok) {
-            to_f32(bP, pl.b32, pl.w[1].p(), pl.e32.p(), st);
-            schur(pl.b32, clover, dag, pl.e32.p(), pl.m32.p(), pl.tmp32.p(), st);
-            defect_update(b64, pl.b32, pl.r_s.p(), pl.m32.p(), sc64, pl.rb, st);
-            for (int s = 0; s < n; ++s)
-                if (active[s]) drift[s] += eps32 * std::sqrt(std::max(rr_e[s], 0.0));
-            read_rr(rr_e);
-            have_full = false;
-        } else {
-            schur_residual();
-        }
+        pl.whole_warm = true;
     }
+    read_state();
+    std::vector<double> rr_e(n), rr_o(n), true_res(n);
+    std::vector<int> outer(n), inner_it(n), conv(n), status(n);
+    for (int s = 0; s < n; ++s) {
+        rr_e[s] = hod[s].rr_e;
+        rr_o[s] = hod[s].rr_o;
+        true_res[s] = hod[s].true_res;
+        outer[s] = hod[s].outer;
+        inner_it[s] = hod[s].inner_it;
+        conv[s] = hod[s].conv;
+        status[s] = hod[s].status;
+    }
+    bool have_full = hoc.have_full != 0;
     if (!have_full) {
-        full_residual();
+        full_kernels(st);
+        read_state();
+        for (int s = 0; s < n; ++s) {
+            rr_e[s] = hod[s].rr_e;
+            rr_o[s] = hod[s].rr_o;
+        }
+        have_full = true;
         for (int s = 0; s < n; ++s) {
             if (status[s] != BPP_OK || bnorm2[s] == 0.0) continue;
             true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);

@@ -15,17 +15,25 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-def test_graph_equals_eager():
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("csw", [0.0, 1.0])
+def test_graph_equals_eager(solver, csw):
+    """Host-driven loops, the inner-loop graph and the whole-solve graph (first
+    call host-driven, then replayed) give bit-identical results."""
     bpp = lib()
     L = (6, 6, 6, 10)
     g, U = gauge(L)
+    if csw:
+        g.clover_build(0.12, csw)
     b = to_dev(synth.gaussian_spinor(L, seed=2))
     for inner in [bpp.F32, bpp.F16, bpp.F64]:
-        xe, se = bpp.solve(g, b, 0.12, 0.0, TOL, bpp.solve_opts(inner_prec=inner, use_graph=False))
-        xg, sg = bpp.solve(g, b, 0.12, 0.0, TOL, bpp.solve_opts(inner_prec=inner, use_graph=True))
-        xg2, _ = bpp.solve(g, b, 0.12, 0.0, TOL, bpp.solve_opts(inner_prec=inner, use_graph=True))
-        assert torch.equal(xe, xg) and torch.equal(xg, xg2)
-        assert se[0]["inner_iters"] == sg[0]["inner_iters"]
+        xe, se = bpp.solve(g, b, 0.12, csw, TOL, bpp.solve_opts(solver=solver, inner_prec=inner, use_graph=0))
+        for mode in (1, 2, 2, 2):
+            xg, sg = bpp.solve(g, b, 0.12, csw, TOL, bpp.solve_opts(solver=solver, inner_prec=inner, use_graph=mode))
+            assert torch.equal(xe, xg), (inner, mode)
+            assert se[0]["inner_iters"] == sg[0]["inner_iters"]
+            assert se[0]["outer_iters"] == sg[0]["outer_iters"]
+            assert sg[0]["converged"] == 1
 
 
 def test_uneven_batch_matches_single():
@@ -38,8 +46,9 @@ def test_uneven_batch_matches_single():
         gs.append(g)
         Us.append(U)
         bs.append(to_dev(synth.gaussian_spinor(L, seed=2 + i)))
-    for inner in [bpp.F32, bpp.F16]:
-        opts = bpp.solve_opts(inner_prec=inner)
+    for inner, mode in [(bpp.F32, 1), (bpp.F16, 1), (bpp.F32, 2), (bpp.F16, 2)]:
+        opts = bpp.solve_opts(inner_prec=inner, use_graph=mode)
+        bpp.solve_batch(gs, bs, kappas, TOL, opts)          # first call of a configuration: host-driven
         xs, st = bpp.solve_batch(gs, bs, kappas, TOL, opts)
         for i, L in enumerate(lats):
             x1, s1 = bpp.solve(gs[i], bs[i], kappas[i], 0.0, TOL, opts)
