@@ -60,7 +60,9 @@ enum {
     BPP_ERR_OOM = -4,           /* device allocation failed */
     BPP_ERR_NOT_CONVERGED = -5, /* solver hit max iterations or broke down; x is the best iterate */
     BPP_ERR_NONFINITE = -6,     /* NaN or Inf met in an input or a residual */
-    BPP_ERR_TIMEOUT = -7        /* a bounded device-side wait ran out */
+    BPP_ERR_TIMEOUT = -7        /* reserved: a bounded device-side wait ran out (the library's
+                                   loops are graph conditionals with iteration caps and it has
+                                   no device-side waits, so this is not returned today) */
 };
 
 /* BPP_F64DF: FP64 values (complex128 at the boundary) with double-float
@@ -225,12 +227,13 @@ int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, dou
               const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream);
 
 /* Batched solve over nlat independent lattices (each with its own gauge
- * handle, hopping parameter and one right-hand side; Wilson, csw = 0), run
- * together so every kernel launch covers all lattices.  b[i], x[i]: device
- * complex128 [V_i][4][3].  stats: NULL or nlat entries.
+ * handle, hopping parameter kappa[i] and one right-hand side), run together so
+ * every kernel launch covers all lattices.  csw != 0: Wilson-clover, each
+ * gauge handle must hold its clover term built with (kappa[i], csw).
+ * b[i], x[i]: device complex128 [V_i][4][3].  stats: NULL or nlat entries.
  * Errors: as bpp_solve. */
 int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* const* x,
-                    const double* kappa, double tol, const bpp_solve_opts* opts,
+                    const double* kappa, double csw, double tol, const bpp_solve_opts* opts,
                     bpp_solve_stats* stats, bpp_stream stream);
 
 /* Link gradient of L = Re<eta, D^{-1} b> for the Wilson hopping term, given

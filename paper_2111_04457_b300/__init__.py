@@ -78,7 +78,7 @@ _SIGS = {
     "bpp_dirac_apply": ([_p, _p, _p, _d, _d, _i, _i, _p], _i),
     "bpp_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
     "bpp_solve": ([_p, _p, _p, _d, _d, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
-    "bpp_solve_batch": ([_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_d), _d,
+    "bpp_solve_batch": ([_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_d), _d, _d,
                          ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_force": ([_p, _p, _p, _d, _p, _i, _p], _i),
     "bpp_launch_count": ([_i], _i64),
@@ -324,8 +324,9 @@ def solve(g: Gauge, b: torch.Tensor, kappa: float, csw: float = 0.0, tol: float 
 
 
 def solve_batch(gauges, bs, kappas, tol: float = 1e-10, opts: SolveOpts = None, xs=None, stream=None,
-                raise_on_fail: bool = True):
-    """Independent Wilson solves on several lattices run together in every launch."""
+                raise_on_fail: bool = True, csw: float = 0.0):
+    """Independent solves on several lattices run together in every launch
+    (csw != 0: each gauge holds its clover term for its own kappa and this csw)."""
     n = len(gauges)
     xs = [torch.empty_like(b) for b in bs] if xs is None else xs
     for b in bs:
@@ -336,7 +337,7 @@ def solve_batch(gauges, bs, kappas, tol: float = 1e-10, opts: SolveOpts = None, 
     K = (_d * n)(*[float(k) for k in kappas])
     o = opts if opts is not None else solve_opts()
     st = (SolveStats * n)()
-    rc = _lib.bpp_solve_batch(n, H, B, X, K, float(tol), ctypes.byref(o), st, _stream(stream))
+    rc = _lib.bpp_solve_batch(n, H, B, X, K, float(csw), float(tol), ctypes.byref(o), st, _stream(stream))
     stats = [s.as_dict() for s in st]
     if raise_on_fail:
         _check(rc)

@@ -304,7 +304,7 @@ int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, dou
 }
 
 int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* const* x, const double* kappa,
-                    double tol, const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream) {
+                    double csw, double tol, const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream) {
     return guard("bpp_solve_batch", [&]() -> int {
         BPP_REQUIRE(nlat >= 1 && nlat <= MAXSYS && U && b && x && kappa, BPP_ERR_INVALID_ARG, "bad batch arguments");
         bpp_solve_opts o;
@@ -316,6 +316,7 @@ int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* co
         std::vector<void*> xv(nlat);
         for (int i = 0; i < nlat; ++i) {
             check_gauge(U[i]);
+            check_clover(*U[i], kappa[i], csw);
             BPP_REQUIRE(b[i] && x[i] && is_device_ptr(b[i]) && is_device_ptr(x[i]), BPP_ERR_INVALID_ARG,
                         "batched solve fields must be device pointers");
             G[i] = U[i];
@@ -323,7 +324,7 @@ int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* co
             bv[i] = b[i];
             xv[i] = x[i];
         }
-        int rc = solve_batch(G, k, false, bv, xv, tol, o, stats, reinterpret_cast<cudaStream_t>(stream));
+        int rc = solve_batch(G, k, csw != 0.0, bv, xv, tol, o, stats, reinterpret_cast<cudaStream_t>(stream));
         if (rc != BPP_OK) return fail(rc, "bpp_solve_batch: a lattice did not reach the tolerance (see stats)");
         return BPP_OK;
     });

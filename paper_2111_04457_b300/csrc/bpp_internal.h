@@ -386,6 +386,8 @@ bool thread_capturing();
 void add_hop_work(int prec, int64_t launches, double bytes);
 void capture_hop_work(int prec, int sys, double bytes);
 void capture_work_reset(int nsys);
+void capture_hop_launch(int prec);
+int64_t capture_hop_launches(int prec);
 const std::vector<double>& capture_work_bytes(int prec);
 int64_t capture_launches();
 // True while `s` is being captured into a CUDA graph.

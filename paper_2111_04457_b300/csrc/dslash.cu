@@ -547,6 +547,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     BPP_CHECK_LAUNCH();
     if (thread_capturing()) {
         for (int s = 0; s < b.nsys(); ++s) capture_hop_work(P, s, per_sys[s]);
+        capture_hop_launch(P);
     } else {
         add_hop_work(P, 1, bytes);
     }

@@ -24,6 +24,7 @@ static int64_t g_work_n[NPREC] = {};
 static double g_work_bytes[NPREC] = {};
 static thread_local std::vector<double> t_cap_bytes[NPREC];
 static thread_local int64_t t_cap_launches = 0;
+static thread_local int64_t t_cap_hops[NPREC] = {};
 
 void add_hop_work(int prec, int64_t launches, double bytes) {
     std::lock_guard<std::mutex> lk(g_work_mu);
@@ -36,8 +37,11 @@ void capture_hop_work(int prec, int sys, double bytes) {
 }
 void capture_work_reset(int nsys) {
     for (auto& v : t_cap_bytes) v.assign(nsys, 0.0);
+    for (auto& h : t_cap_hops) h = 0;
     t_cap_launches = 0;
 }
+void capture_hop_launch(int prec) { t_cap_hops[prec] += 1; }
+int64_t capture_hop_launches(int prec) { return t_cap_hops[prec]; }
 const std::vector<double>& capture_work_bytes(int prec) { return t_cap_bytes[prec]; }
 int64_t capture_launches() { return t_cap_launches; }
 

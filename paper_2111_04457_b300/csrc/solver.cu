@@ -101,6 +101,7 @@ struct Plan {
     bool whole_warm = false;             // one host-driven solve ran (every branch kernel tuned)
     std::vector<double> w_iter_bytes;    // per system, inner precision
     double w_full_bytes[NPREC] = {}, w_rel_bytes[NPREC] = {}, w_schur_bytes[NPREC] = {};
+    int64_t w_full_hops[NPREC] = {}, w_rel_hops[NPREC] = {}, w_schur_hops[NPREC] = {}, w_iter_hops = 0;
     int64_t w_full_launch = 0, w_rel_launch = 0, w_schur_launch = 0, w_iter_launch = 0;
     int64_t w_inner_launch = 0, w_pass_launch = 0;
     size_t bytes = 0;
@@ -401,6 +402,7 @@ static void capture_body(cudaGraph_t body, F f) {
 
 struct CapSnap {
     double bytes[NPREC];
+    int64_t hops[NPREC];
     int64_t launches;
 };
 static CapSnap cap_snap(int n) {
@@ -409,6 +411,7 @@ static CapSnap cap_snap(int n) {
         c.bytes[p] = 0.0;
         const auto& v = capture_work_bytes(p);
         for (int s = 0; s < n && s < (int)v.size(); ++s) c.bytes[p] += v[s];
+        c.hops[p] = capture_hop_launches(p);
     }
     c.launches = capture_launches();
     return c;
@@ -618,7 +621,10 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                     const CapSnap p1 = cap_snap(n);
                     capture_body(add_conditional(s1, h_check, cudaGraphCondTypeIf, 1)[0], full_kernels);
                     const CapSnap p2 = cap_snap(n);
-                    for (int q = 0; q < NPREC; ++q) pl.w_full_bytes[q] = p2.bytes[q] - p1.bytes[q];
+                    for (int q = 0; q < NPREC; ++q) {
+                        pl.w_full_bytes[q] = p2.bytes[q] - p1.bytes[q];
+                        pl.w_full_hops[q] = p2.hops[q] - p1.hops[q];
+                    }
                     pl.w_full_launch = p2.launches - p1.launches;
                     capture_body(add_conditional(s1, h_inner, cudaGraphCondTypeIf, 1)[0], [&](cudaStream_t s2) {
                         const unsigned long long h_split = new_handle(s2, 0), h_branch = new_handle(s2, 0);
@@ -652,6 +658,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                                                      (s < (int)before.size() ? before[s] : 0.0);
                         }
                         pl.w_iter_launch = i2.launches - i1.launches;
+                        pl.w_iter_hops = i2.hops[bP.prec] - i1.hops[bP.prec];
                         outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, s2, split ? pl.xe_s.p() : nullptr);
                         oc_decide(od, oc, scP, h_branch, s2);
                         const CapSnap i3 = cap_snap(n);
@@ -668,6 +675,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                         for (int q = 0; q < NPREC; ++q) {
                             pl.w_rel_bytes[q] = b2.bytes[q] - b1.bytes[q];
                             pl.w_schur_bytes[q] = b3.bytes[q] - b2.bytes[q];
+                            pl.w_rel_hops[q] = b2.hops[q] - b1.hops[q];
+                            pl.w_schur_hops[q] = b3.hops[q] - b2.hops[q];
                         }
                         pl.w_rel_launch = b2.launches - b1.launches;
                         pl.w_schur_launch = b3.launches - b2.launches;
@@ -700,9 +709,12 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         // system, and every executed branch for all systems
         for (int q = 0; q < NPREC; ++q) {
             double by = hoc.n_full * pl.w_full_bytes[q] + hoc.n_rel * pl.w_rel_bytes[q] + hoc.n_schur * pl.w_schur_bytes[q];
-            if (q == bP.prec)
+            int64_t hops = hoc.n_full * pl.w_full_hops[q] + hoc.n_rel * pl.w_rel_hops[q] + hoc.n_schur * pl.w_schur_hops[q];
+            if (q == bP.prec) {
                 for (int s = 0; s < n; ++s) by += hod[s].inner_it * pl.w_iter_bytes[s];
-            if (by > 0) add_hop_work(q, 0, by);
+                hops += (int64_t)loops[1] * pl.w_iter_hops;
+            }
+            if (by > 0 || hops > 0) add_hop_work(q, hops, by);
         }
         count_launch((int64_t)hoc.passes * pl.w_pass_launch + (int64_t)hoc.n_inner * pl.w_inner_launch +
                      (int64_t)loops[1] * pl.w_iter_launch + (int64_t)hoc.n_full * pl.w_full_launch +

@@ -79,3 +79,23 @@ def test_launch_count_grows():
     bpp.solve(g, b, 0.12, 0.0, TOL)
     n = bpp.launch_count()
     assert n > 10
+
+
+def test_clover_batch_uneven():
+    """Wilson-clover lattices of different sizes and kappas in one batched solve."""
+    bpp = lib()
+    lats = [(4, 4, 4, 4), (6, 4, 4, 8), (4, 6, 6, 6)]
+    kappas = synth.uniform_kappas(len(lats))
+    csw = 1.0
+    gs, Us, bs, Fs = [], [], [], []
+    for i, L in enumerate(lats):
+        g, U = gauge(L, seed=3 + i)
+        g.clover_build(kappas[i], csw)
+        gs.append(g)
+        Us.append(U)
+        Fs.append(oracle.clover_field(U, kappas[i], csw, L))
+        bs.append(to_dev(synth.gaussian_spinor(L, seed=7 + i)))
+    for inner in (bpp.F32, bpp.F16):
+        xs, st = bpp.solve_batch(gs, bs, kappas, TOL, bpp.solve_opts(inner_prec=inner), csw=csw)
+        for i, L in enumerate(lats):
+            assert oracle.true_residual(Us[i], to_np(bs[i]), to_np(xs[i]), kappas[i], L, BC, Fs[i]) <= TOL
