@@ -310,6 +310,16 @@ def run_ours(args, rank, world):
                "frac": (df_gbs / peak_hbm) if df_gbs else None, "traffic": None,
                "kernel": "k_hop double-float (outer defects, FP32 pipe)", "peak_kind": peak_kind,
                "launches": nd, "avg_us": 1000 * msd / max(nd, 1), "share_ms": msd}
+    # DRAM traffic per launch of the inner hopping kernel, from the committed
+    # ncu capture of this workload (null when the capture does not match)
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_hop_f16_32x64_in_solve.json")) as f:
+            cap = json.load(f)
+        if inner == bpp.F16 and list(L) == cap["lattice"]:
+            roof_inner["traffic"] = cap["traffic_bytes_per_launch"]
+            roof_inner["traffic_source"] = "profiles/k_hop_f16_32x64_in_solve.md"
+    except (OSError, KeyError, ValueError):
+        pass
     dominant = max([roof_f64, roof_inner, roof_df], key=lambda r: r["share_ms"])
 
     # e2e: host pinned b -> solve (library copies in and out) -> host x
