@@ -2,6 +2,7 @@
 #include <string>
 
 #include "blas.h"
+#include "clover_dev.h"
 #include "kernels.h"
 #include "reduce.h"
 
@@ -579,6 +580,60 @@ void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) { launch_o
 
 void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st) {
     launch_outer(k_f64_to_split, b64, const_cast<char*>(in), out, nullptr, st);
+}
+
+// Odd half of the final check, all FP64: with h = kappa H_oe x_e (op.b) and
+// y = b_o + h, x_o = A_oo^-1 y (Wilson: y) is written to op.c and the odd
+// residual b_o - (A_oo x_o - h) of the full D is reduced into sc.rr.
+template <bool CLOVER>
+__global__ void __launch_bounds__(BLAS_B) k_odd_reconstruct(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    double red[4] = {0, 0, 0, 0};
+    if (i < d.g.Vh) {
+        cx<double> b[12], h[12], y[12], x[12], ax[12];
+        Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, b);
+        Access<P64>::load_spinor(sys_view<P64>(op.b, d), i, h);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] = b[k] + h[k];
+        if (CLOVER) {
+            clover_apply_site<P64>(d.Ainv[1], i, y, x);
+            clover_apply_site<P64>(d.A[1], i, x, ax);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) x[k] = ax[k] = y[k];
+        }
+        Access<P64>::store_spinor(sys_view<P64>(op.c, d), i, x);
+        cx<double> r[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r[k] = b[k] - (ax[k] - h[k]);
+        red[0] = norm12(r);
+    }
+    double tot[4];
+    if (!reduce_sys<4, double>(RedCtx{op.map, op.partials, op.tickets}, s, red, tot)) return;
+    if (threadIdx.x == 0) op.sc[s].rr = tot[0];
+}
+
+void odd_reconstruct(const Batch& b64, bool clover, const char* bo, const char* h, char* xo, KScal* sc, RedBuf& rb,
+                     cudaStream_t st) {
+    OuterParams op;
+    op.s64 = b64.dev();
+    op.sP = b64.dev();
+    int nb = 0;
+    op.map = block_map(b64, BLAS_B, nb);
+    rb.ensure(nb, b64.nsys(), st);
+    op.a = const_cast<char*>(bo);
+    op.b = const_cast<char*>(h);
+    op.c = xo;
+    op.sc = sc;
+    op.partials = rb.partials.as<double>();
+    op.tickets = rb.tickets.as<unsigned>();
+    if (clover) k_odd_reconstruct<true><<<nb, BLAS_B, 0, st>>>(op);
+    else k_odd_reconstruct<false><<<nb, BLAS_B, 0, st>>>(op);
+    count_launch();
+    BPP_CHECK_LAUNCH();
 }
 
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {

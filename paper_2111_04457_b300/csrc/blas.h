@@ -84,6 +84,10 @@ void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaS
 // ||r_s||^2 and ||r_s|| in the scalars (scale is read before it is replaced)
 void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m32, KScal* sc, RedBuf& rb,
                    cudaStream_t st);
+// Odd half of the final FP64 check: h = kappa H_oe x_e given, x_o = A_oo^-1
+// (b_o + h) written, ||b_o - (A_oo x_o - h)||^2 into sc.rr
+void odd_reconstruct(const Batch& b64, bool clover, const char* bo, const char* h, char* xo, KScal* sc, RedBuf& rb,
+                     cudaStream_t st);
 // x64 = hi + lo of the split-FP64 vector xs (exact)
 void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st);
 // out = a * in + y (same precision), a per system given on the host

@@ -45,18 +45,18 @@ __global__ void k_oc_classify(OuterDev* od, OuterCtl* oc, unsigned long long h_c
     set_cond(h_inner, inner);
 }
 
-__global__ void k_oc_full_even(OuterDev* od, const KScal* s64, int n) {
+// The odd part of the final check came first (its norm is in the scalars)...
+__global__ void k_oc_full_odd(OuterDev* od, const KScal* s64, int n) {
     if (threadIdx.x != 0) return;
-    for (int s = 0; s < n; ++s) od[s].rr_e = s64[s].rr;
+    for (int s = 0; s < n; ++s) od[s].rr_o = s64[s].rr;
 }
 
-__global__ void k_oc_full_odd(OuterDev* od, OuterCtl* oc, KScal* s64) {
+// ... then the even part, whose norm stays in the scalars for the downcast of
+// a further correction.
+__global__ void k_oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64) {
     if (threadIdx.x != 0) return;
     for (int s = 0; s < oc->n; ++s) {
-        od[s].rr_o = s64[s].rr;
-        // the odd norm replaced the even one in the scalars: restore it for the
-        // downcast of the next correction
-        s64[s].rr = od[s].rr_e;
+        od[s].rr_e = s64[s].rr;
         s64[s].scale = sqrt(fmax(od[s].rr_e, 0.0));
     }
     oc->have_full = 1;
@@ -152,11 +152,11 @@ __global__ void k_oc_loop(OuterCtl* oc, unsigned long long h_outer) {
 void oc_classify(OuterDev* od, OuterCtl* oc, unsigned long long hc, unsigned long long hi, cudaStream_t st) {
     OC_LAUNCH(k_oc_classify<<<1, 32, 0, st>>>(od, oc, hc, hi));
 }
-void oc_full_even(OuterDev* od, const KScal* s64, int n, cudaStream_t st) {
-    OC_LAUNCH(k_oc_full_even<<<1, 32, 0, st>>>(od, s64, n));
+void oc_full_odd(OuterDev* od, const KScal* s64, int n, cudaStream_t st) {
+    OC_LAUNCH(k_oc_full_odd<<<1, 32, 0, st>>>(od, s64, n));
 }
-void oc_full_odd(OuterDev* od, OuterCtl* oc, KScal* s64, cudaStream_t st) {
-    OC_LAUNCH(k_oc_full_odd<<<1, 32, 0, st>>>(od, oc, s64));
+void oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64, cudaStream_t st) {
+    OC_LAUNCH(k_oc_full_even<<<1, 32, 0, st>>>(od, oc, s64));
 }
 void oc_inner_setup(OuterDev* od, OuterCtl* oc, KScal* s64, KScal* sP, unsigned long long hs, cudaStream_t st) {
     OC_LAUNCH(k_oc_inner_setup<<<1, 32, 0, st>>>(od, oc, s64, sP, hs));

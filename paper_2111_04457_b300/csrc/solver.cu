@@ -517,21 +517,16 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
 
     // the branch kernel sequences (host-driven and captured alike)
     auto full_kernels = [&](cudaStream_t cs) {
-        // x_o = A_oo^-1 (b_o + kappa H_oe x_e) (double-float when split, then its
-        // exact FP64 value); De = A_ee x_e - kappa H_eo x_o; Do = A_oo x_o - kappa H_oe x_e
-        // in FP64: the true residual of the returned x
-        if (split) {
-            hop(b64s, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe_s.p(), pl.tmpo_s.p(), pl.bo_s.p(), cs);
-            split_to_f64(b64, pl.tmpo_s.p(), pl.xo.p(), cs);
-        } else {
-            hop(b64, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe.p(), pl.xo.p(), pl.bo.p(), cs);
-        }
+        // The true residual of the returned x with the full FP64 D: h = kappa
+        // H_oe x_e once, x_o = A_oo^-1 (b_o + h) and the odd residual
+        // b_o - (A_oo x_o - h) from it, then De = A_ee x_e - kappa H_eo x_o and
+        // the even residual b_e - De.
+        hop(b64, 1, dag, HOP_PLAIN, +1.0, pl.xe.p(), pl.tmpo.p(), nullptr, cs);
+        odd_reconstruct(b64, clover, pl.bo.p(), pl.tmpo.p(), pl.xo.p(), sc64, pl.rb, cs);
+        oc_full_odd(od, sc64, n, cs);
         hop(b64, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xo.p(), pl.r.p(), pl.xe.p(), cs);
         outer_residual(b64, pl.be.p(), pl.r.p(), sc64, pl.rb, cs);
-        oc_full_even(od, sc64, n, cs);
-        hop(b64, 1, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.xe.p(), pl.tmpo.p(), pl.xo.p(), cs);
-        outer_residual(b64, pl.bo.p(), pl.tmpo.p(), sc64, pl.rb, cs);
-        oc_full_odd(od, oc, sc64, cs);
+        oc_full_even(od, oc, sc64, cs);
     };
     auto reliable_kernels = [&](cudaStream_t cs) {
         to_f32(bP, pl.b32, pl.w[1].p(), pl.e32.p(), cs);
