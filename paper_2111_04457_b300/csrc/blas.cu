@@ -137,6 +137,10 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
     } else if (OP == B_NORM2) {
         A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
         red[0] += norm12(a);
+    } else if (OP == B_NORM2X2) {
+        A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.r, d), i, b);
+        red[0] += norm12(a) + norm12(b);
     }
 }
 
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     map_block(bp.map, s, tile);
     const SysDesc& d = bp.sys[s];
     KScal* K = bp.sc + s;
-    const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2) || !K->done;
+    const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2 || OP == B_NORM2X2) || !K->done;
     // scalars used by the update (read before any finalize of this launch)
     const double2 al = K->alpha, om = K->omega, be = K->beta;
     using real = typename PT<P>::real;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     } else if (OP == B_CG_BETA) {
         k.beta = c2(k.zz > 0.0 ? tot[0] / k.zz : 0.0, 0.0);
         k.zz = tot[0];
-    } else if (OP == B_NORM2) {
+    } else if (OP == B_NORM2 || OP == B_NORM2X2) {
         k.bb = tot[0];
     }
 }
@@ -268,6 +272,7 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
             k_cg_p<P><<<nb, BLAS_B, 0, st>>>(bp);
             break;
         case B_NORM2: k_blas<P, B_NORM2><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_NORM2X2: k_blas<P, B_NORM2X2><<<nb, BLAS_B, 0, st>>>(bp); break;
         default: throw Error(BPP_ERR_INVALID_ARG, "bad blas op");
     }
     count_launch();
@@ -546,6 +551,27 @@ __global__ void __launch_bounds__(BLAS_B) k_scale_f64(OuterParams op) {
     Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
 }
 
+// v (op.a) *= scale in place (FP64) and op.b = its split-FP64 copy (op.b may be null).
+__global__ void __launch_bounds__(BLAS_B) k_scale_split(OuterParams op) {
+    int s, tile;
+    map_block(op.map, s, tile);
+    const SysDesc& d = op.s64[s];
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= d.g.Vh) return;
+    const double f = op.sc[s].scale;
+    cx<double> v[12];
+    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = f * v[k];
+    Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
+    if (op.b) {
+        cx<df64> w[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = mkc(df64(v[k].r), df64(v[k].i));
+        Access<P64S>::store_spinor(sys_view<P64S>(op.b, d), i, w);
+    }
+}
+
 // split-FP64 copy (op.b) of an FP64 vector (op.a).
 __global__ void __launch_bounds__(BLAS_B) k_f64_to_split(OuterParams op) {
     int s, tile;
@@ -577,6 +603,10 @@ static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, c
 }
 
 void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) { launch_outer(k_scale_f64, b64, v, nullptr, sc, st); }
+
+void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st) {
+    launch_outer(k_scale_split, b64, v, out, sc, st);
+}
 
 void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st) {
     launch_outer(k_f64_to_split, b64, const_cast<char*>(in), out, nullptr, st);

@@ -35,7 +35,7 @@ double hop_bytes_per_site(int prec, int mode);
 void full_to_eo(const Batch& b, int sys0, int nsys, const void* canon, int canon_f64, int64_t canon_sys_stride,
                 char* even, char* odd, int gamma5, cudaStream_t st);
 void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char* odd, void* canon, int canon_f64,
-                int64_t canon_sys_stride, int gamma5, cudaStream_t st);
+                int64_t canon_sys_stride, int gamma5, cudaStream_t st, double scale = 1.0);
 // Half canonical fields [nsys][Vh][4][3] <-> internal half fields.
 void half_to_int(const Batch& b, const void* canon, int canon_f64, char* out, cudaStream_t st);
 void int_to_half(const Batch& b, const char* in, void* canon, int canon_f64, cudaStream_t st);

@@ -54,7 +54,7 @@ __global__ void k_full_to_eo(const SysDesc* sys, int sys0, const TC* __restrict_
 
 template <int P, class TC>
 __global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, const char* odd, TC* canon,
-                             int64_t cstride, int g5) {
+                             int64_t cstride, int g5, double scale) {
     using real = typename PT<P>::real;
     const SysDesc& d = sys[sys0 + blockIdx.y];
     const Geom g = d.g;
@@ -68,6 +68,11 @@ __global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, con
     cx<real> v[12];
     Access<P>::load_spinor(sys_view<P>(const_cast<char*>(p == 0 ? even : odd), d), i, v);
     TC* dst = canon + blockIdx.y * cstride + lex * 12;
+    if (scale != 1.0) {
+        const real f = (real)scale;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = f * v[k];
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>((g5 && k < 6) ? -v[k] : v[k]);
 }
@@ -122,14 +127,14 @@ void full_to_eo(const Batch& b, int sys0, int nsys, const void* canon, int canon
 }
 
 void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char* odd, void* canon, int canon_f64,
-                int64_t cstride, int g5, cudaStream_t st) {
+                int64_t cstride, int g5, cudaStream_t st, double scale) {
     const int B = 256;
     dim3 grid((unsigned)((2 * (int64_t)b.Vh_max + B - 1) / B), nsys);
     BPP_PREC_DISPATCH(b.prec, {
         if (canon_f64)
-            k_eo_to_full<PP, double2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<double2*>(canon), cstride, g5);
+            k_eo_to_full<PP, double2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<double2*>(canon), cstride, g5, scale);
         else
-            k_eo_to_full<PP, float2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<float2*>(canon), cstride, g5);
+            k_eo_to_full<PP, float2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<float2*>(canon), cstride, g5, scale);
     });
     count_launch();
     BPP_CHECK_LAUNCH();

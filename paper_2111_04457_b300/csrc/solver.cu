@@ -448,13 +448,10 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     {
         BlasVecs v;
         v.x = pl.be.p();
-        blas(b64, B_NORM2, v, sc64, pl.rb, st);
+        v.r = pl.bo.p();
+        blas(b64, B_NORM2X2, v, sc64, pl.rb, st);
         read_scalars(pl.d64, h64, st);
         for (int s = 0; s < n; ++s) bnorm2[s] = h64[s].bb;
-        v.x = pl.bo.p();
-        blas(b64, B_NORM2, v, sc64, pl.rb, st);
-        read_scalars(pl.d64, h64, st);
-        for (int s = 0; s < n; ++s) bnorm2[s] += h64[s].bb;
     }
     for (int s = 0; s < n; ++s)
         BPP_REQUIRE(std::isfinite(bnorm2[s]), BPP_ERR_NONFINITE, "non-finite right-hand side");
@@ -469,12 +466,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         h64[s].scale = 1.0 / bscale[s];
     }
     write_scalars(pl.d64, h64, st);
-    scale_f64(b64, pl.be.p(), sc64, st);
-    scale_f64(b64, pl.bo.p(), sc64, st);
-    if (split) {
-        f64_to_split(b64, pl.be.p(), pl.be_s.p(), st);
-        f64_to_split(b64, pl.bo.p(), pl.bo_s.p(), st);
-    }
+    scale_split(b64, pl.be.p(), split ? pl.be_s.p() : nullptr, sc64, st);
+    scale_split(b64, pl.bo.p(), split ? pl.bo_s.p() : nullptr, sc64, st);
     // bhat = b_e + kappa H_eo A_oo^-1 b_o (double-float when split)
     {
         const Batch& bb = split ? b64s : b64;
@@ -494,8 +487,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     bool x_zero = !o.use_x0;
     if (o.use_x0) {
         for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
-        scale_f64(b64, pl.xe.p(), sc64, st);
-        if (split) f64_to_split(b64, pl.xe.p(), pl.xe_s.p(), st);
+        scale_split(b64, pl.xe.p(), split ? pl.xe_s.p() : nullptr, sc64, st);
     } else {
         BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
         if (split) BPP_CUDA(cudaMemsetAsync(pl.xe_s.p(), 0, b64s.vec_bytes, st));
@@ -767,11 +759,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
             if (status[s] == BPP_OK && bnorm2[s] > 0.0) true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);
     }
     // x = ||b|| x'
-    for (int s = 0; s < n; ++s) h64[s].scale = bscale[s];
-    write_scalars(pl.d64, h64, st);
-    scale_f64(b64, pl.xe.p(), sc64, st);
-    scale_f64(b64, pl.xo.p(), sc64, st);
-    for (int s = 0; s < n; ++s) eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st);
+    for (int s = 0; s < n; ++s)
+        eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st, bscale[s]);
     BPP_CUDA(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int rc = BPP_OK;
