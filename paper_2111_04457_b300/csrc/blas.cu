@@ -9,7 +9,10 @@
 namespace bpp {
 
 constexpr int BLAS_B = 256;
-constexpr int BLAS_SPT = 4;   // sites per thread
+#ifndef BPP_BLAS_SPT
+#define BPP_BLAS_SPT 8
+#endif
+constexpr int BLAS_SPT = BPP_BLAS_SPT;   // sites per thread
 
 void RedBuf::ensure(int nblocks, int nsys, cudaStream_t st) {
     if (nblocks > cap_blocks) {

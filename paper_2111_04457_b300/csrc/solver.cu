@@ -436,7 +436,6 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     const Batch& bP = pl.bP;
     KScal* sc64 = pl.d64.as<KScal>();
     std::vector<KScal>& h64 = pl.h64;
-    std::vector<KScal>& hP = pl.hP;
     pl.rb.ensure(1, n, st);   // tickets
 
     // b -> even/odd FP64 (gamma5 b for the adjoint solve)
