@@ -228,7 +228,10 @@ template <> struct Access<P64S> {
     static __device__ __forceinline__ void store_spinor(const SpinorView& f, int64_t i, const cx<df64> s[12]) {
         float4* p = static_cast<float4*>(f.data);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) p[k * f.stride + i] = make_float4(s[k].r.hi, s[k].r.lo, s[k].i.hi, s[k].i.lo);
+        for (int k = 0; k < 12; ++k) {
+            const df64 r = normalized(s[k].r), m = normalized(s[k].i);
+            p[k * f.stride + i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+        }
     }
     static __device__ __forceinline__ void load_link(const LinkView& u, int64_t i, cx<df64> m[9]) {
         const float4* p = static_cast<const float4*>(u.data);

@@ -8,8 +8,8 @@
 // Building blocks are the error-free transformations of Knuth (TwoSum) and
 // Dekker (FastTwoSum), with the product error taken from a fused multiply-add
 // (TwoProd).  Addition is the cheaper variant that adds the two low parts into
-// the error term (relative error ~2^-44 of the larger operand), which is ample
-// for defects down to 1e-12 relative.
+// the error term (relative error ~2^-44 of the larger operand) and does not
+// renormalise (see operator+), which is ample for defects down to 1e-12.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -56,10 +56,16 @@ __device__ __forceinline__ df64 two_sum(float a, float b) {
     return df64(s, (a - (s - bb)) + (b - bb));
 }
 
+// Addition leaves the result unnormalised: (TwoSum of the high parts, its
+// error plus both low parts).  hi + lo is the sum to ~2^-48 as before; |lo| may
+// exceed half an ulp of hi, which products (TwoProd with both cross terms) and
+// further additions tolerate.  Products, fma and stores renormalise.
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
     const df64 s = two_sum(a.hi, b.hi);
-    return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+    return df64(s.hi, s.lo + (a.lo + b.lo));
 }
+
+__device__ __forceinline__ df64 normalized(df64 a) { return quick_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 

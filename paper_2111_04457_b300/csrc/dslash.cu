@@ -192,6 +192,48 @@ __device__ __forceinline__ void hop_term_dec(cx<real> acc[12], const cx<real> ps
     reconstruct<MU, S>(acc, g);
 }
 
+// Double-float g = U h (or U^dag h): each output component is a sum of six
+// products, accumulated lazily -- exact products (TwoProd via FMA, cross terms
+// of the low parts), one TwoSum chain on the high parts and plain FP32 sums of
+// all error terms -- with a single renormalisation at the end.
+__device__ __forceinline__ void df_prod(df64 a, df64 b, float& p, float& e) {
+    p = a.hi * b.hi;
+    e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+}
+__device__ __forceinline__ void df_lazy_add(float& S, float& E, float p, float e) {
+    const float s = S + p;
+    const float bb = s - S;
+    E += ((S - (s - bb)) + (p - bb)) + e;
+    S = s;
+}
+template <bool BACK>
+__device__ __forceinline__ void link_mul(const cx<df64> U[9], const cx<df64> h[6], cx<df64> g[6]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f, p, e;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const cx<df64> u = BACK ? U[3 * b + a] : U[3 * a + b];
+                const cx<df64> x = h[3 * s + b];
+                // re += u.r x.r - u.i x.i  (U^dag: + u.i x.i)
+                df_prod(u.r, x.r, p, e);
+                if (b == 0) { Sr = p; Er = e; } else df_lazy_add(Sr, Er, p, e);
+                df_prod(u.i, x.i, p, e);
+                if (BACK) df_lazy_add(Sr, Er, p, e); else df_lazy_add(Sr, Er, -p, -e);
+                // im += u.r x.i + u.i x.r  (U^dag: - u.i x.r)
+                df_prod(u.r, x.i, p, e);
+                if (b == 0) { Si = p; Ei = e; } else df_lazy_add(Si, Ei, p, e);
+                df_prod(u.i, x.r, p, e);
+                if (BACK) df_lazy_add(Si, Ei, -p, -e); else df_lazy_add(Si, Ei, p, e);
+            }
+            g[3 * s + a] = mkc(quick_two_sum(Sr, Er), quick_two_sum(Si, Ei));
+        }
+}
+
 template <int P, int MU, int S, bool BACK>
 __device__ __forceinline__ void hop_term(cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
     using real = typename PT<P>::real;
