@@ -193,6 +193,15 @@ def cpu_oracle_sample(L, target_s=12.0):
     return total_sites * BYTES_F64 / total_t / 1e9, total_sites, total_t, threads
 
 
+def solve_config(L, inner_name, world=1):
+    """The benchmark workload as reported in `config` (shared by both arms)."""
+    return {"workload": f"Wilson eo-BiCGStab solve, {'x'.join(map(str, L))}, kappa {KAPPA}, 1 Gaussian RHS, "
+                        f"{inner_name} inner + FP64 defect correction to true resid {TOL}",
+            "lattice": list(L), "kappa": KAPPA, "tol": TOL, "rhs": 1,
+            "l2": "inputs larger than L2 (links 1.2 GB FP64 / 0.6 GB FP32 / 0.3 GB FP16); no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -209,11 +218,11 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "Wilson eo-dslash, 32^3x64, random SU(3) links eps=0.3 seed 1, kappa 0.12",
-                      "lattice": list(L)},
+           "config": solve_config(L, "f16-storage/f32" if args.inner == "f16" else "f32"),
            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                            "sample": "FP64 oracle D (Eq. 1, plain C loops, OpenMP) on random site samples of "
-                                      "the 32^3x64 lattice, ~4 s per step; bytes = 1536 B per output site"},
+                            "sample": "the oracle's FP64 D (Eq. 1, plain C loops, OpenMP) on random site samples of "
+                                      "this lattice, ~4 s per step, as the even-odd dslash work of the solve: "
+                                      "1536 B per output site (the oracle's full solve would take hours)"},
            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -387,11 +396,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"{inner_name} inner, f64 outer", "data": "synthetic",
-        "config": {"workload": f"Wilson eo-BiCGStab solve, {'x'.join(map(str, L))}, kappa {KAPPA}, 1 Gaussian RHS, "
-                               f"{inner_name} inner + FP64 defect correction to true resid {TOL}",
-                   "lattice": list(L), "kappa": KAPPA, "tol": TOL, "rhs": 1,
-                   "l2": "inputs larger than L2 (links 1.2 GB FP64 / 0.6 GB FP32 / 0.3 GB FP16); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": solve_config(L, inner_name, world),
         "solve_ms": ms_step,
         "solve_ms_fp64": fp64_ms,
         "solve_ms_f32_inner": f32_ms,
