@@ -206,6 +206,8 @@ typedef struct {
     int status;         /* BPP_OK or the per-RHS error code */
     double true_resid;  /* ||b - D x|| / ||b||, full FP64 D recomputed from scratch */
     double seconds;     /* wall time of the whole call (same for every RHS) */
+    double hop_bytes;   /* algorithmic bytes of every hopping-kernel launch of the call (all RHS) */
+    double hop_gbs;     /* hop_bytes / seconds / 1e9: the dslash GB/s the call sustained */
 } bpp_solve_stats;
 
 /* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 0 (per precision),

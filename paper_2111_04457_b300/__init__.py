@@ -58,7 +58,8 @@ class SolveOpts(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("converged", ctypes.c_int),
-                ("status", ctypes.c_int), ("true_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("status", ctypes.c_int), ("true_resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("hop_bytes", ctypes.c_double), ("hop_gbs", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

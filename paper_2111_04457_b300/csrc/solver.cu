@@ -29,6 +29,8 @@
 
 namespace bpp {
 
+int work_read(int prec, int64_t* n, double* bytes, int reset);
+
 void schur(const Batch& b, bool clover, int dag, char* in_e, char* out_e, char* tmp_o, cudaStream_t st) {
     // tmp_o = A_oo^-1 (-kappa H_oe in);  out_e = A_ee in + kappa H_eo tmp_o
     hop(b, 1, dag, clover ? HOP_INV : HOP_PLAIN, -1.0, in_e, tmp_o, nullptr, st);
@@ -421,6 +423,12 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                 const std::vector<const void*>& b_canon, const std::vector<void*>& x_canon, double tol,
                 const bpp_solve_opts& o, bpp_solve_stats* stats, cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
+    double work0 = 0.0;
+    for (int q = 0; q < NPREC; ++q) {
+        double by = 0.0;
+        work_read(q, nullptr, &by, 0);
+        work0 += by;
+    }
     const int n = (int)G.size();
     BPP_REQUIRE(n >= 1 && n <= MAXSYS, BPP_ERR_INVALID_ARG, "number of systems must be 1..64");
     BPP_REQUIRE(tol > 0.0, BPP_ERR_INVALID_ARG, "tol must be positive");
@@ -762,6 +770,12 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st, bscale[s]);
     BPP_CUDA(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    double work1 = 0.0;
+    for (int q = 0; q < NPREC; ++q) {
+        double by = 0.0;
+        work_read(q, nullptr, &by, 0);
+        work1 += by;
+    }
     int rc = BPP_OK;
     for (int s = 0; s < n; ++s) {
         if (status[s] == BPP_OK && !conv[s]) status[s] = BPP_ERR_NOT_CONVERGED;
@@ -773,6 +787,8 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
             stats[s].status = status[s];
             stats[s].true_resid = true_res[s];
             stats[s].seconds = secs;
+            stats[s].hop_bytes = work1 - work0;
+            stats[s].hop_gbs = secs > 0.0 ? (work1 - work0) / secs / 1e9 : 0.0;
         }
     }
     return rc;
