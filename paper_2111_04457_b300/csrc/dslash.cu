@@ -157,25 +157,27 @@ __device__ __forceinline__ void decode(const Raw<P32>& r, cx<float> psi[12], cx<
     }
     u[8] = mkc(r.u8.x, r.u8.y);
 }
+// The neighbour's per-site scale multiplies the 18 link reals instead of the
+// 24 spinor reals: the hop term is linear in the spinor.
 __device__ __forceinline__ void decode(const Raw<P16>& r, cx<float> psi[12], cx<float> u[9]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float2 a = h2f(r.s[k].x), b = h2f(r.s[k].y), c = h2f(r.s[k].z), d = h2f(r.s[k].w);
-        psi[4 * k + 0] = mkc(a.x * r.sc, a.y * r.sc);
-        psi[4 * k + 1] = mkc(b.x * r.sc, b.y * r.sc);
-        psi[4 * k + 2] = mkc(c.x * r.sc, c.y * r.sc);
-        psi[4 * k + 3] = mkc(d.x * r.sc, d.y * r.sc);
+        psi[4 * k + 0] = mkc(a.x, a.y);
+        psi[4 * k + 1] = mkc(b.x, b.y);
+        psi[4 * k + 2] = mkc(c.x, c.y);
+        psi[4 * k + 3] = mkc(d.x, d.y);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float2 a = h2f(r.u[k].x), b = h2f(r.u[k].y), c = h2f(r.u[k].z), d = h2f(r.u[k].w);
-        u[4 * k + 0] = mkc(a.x, a.y);
-        u[4 * k + 1] = mkc(b.x, b.y);
-        u[4 * k + 2] = mkc(c.x, c.y);
-        u[4 * k + 3] = mkc(d.x, d.y);
+        u[4 * k + 0] = mkc(a.x * r.sc, a.y * r.sc);
+        u[4 * k + 1] = mkc(b.x * r.sc, b.y * r.sc);
+        u[4 * k + 2] = mkc(c.x * r.sc, c.y * r.sc);
+        u[4 * k + 3] = mkc(d.x * r.sc, d.y * r.sc);
     }
     const float2 a = h2f(r.u8);
-    u[8] = mkc(a.x, a.y);
+    u[8] = mkc(a.x * r.sc, a.y * r.sc);
 }
 
 // One hop term: decode, project with (1 + S gamma_MU), colour-multiply
