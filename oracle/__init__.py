@@ -87,6 +87,7 @@ def _load():
         lib.oracle_clover_field_sites.argtypes = [p, p, p, d, d, p, i64, p]
         lib.oracle_clover_leaf.argtypes = [p, p, i, i, i64, p]
         lib.oracle_link_gradient.argtypes = [p, p, p, p, p, d, p]
+        lib.oracle_clover_gradient.argtypes = [p, p, p, p, p, d, d, p]
         _lib = lib
     return _lib
 
@@ -164,12 +165,17 @@ def apply_D_sites_clover(U, psi, kappa, L, csw, sites, bc=DEFAULT_BC, dagger=Fal
     return out
 
 
-def link_gradient(x, lam, kappa, L, bc=DEFAULT_BC):
-    """Unconstrained grad_U of L = Re<eta, D^{-1} b> given x and lam = D^{-dag} eta."""
+def link_gradient(x, lam, kappa, L, bc=DEFAULT_BC, U=None, csw=0.0):
+    """Unconstrained grad_U of L = Re<eta, D^{-1} b> given x and lam = D^{-dag} eta:
+    the hopping term's part, plus the clover term's part when csw != 0 (needs U)."""
     G = np.empty((4, volume(L), 3, 3), dtype=np.complex128)
     x, lam, Lv, bv = _c128(x), _c128(lam), _ivec(L), _ivec(bc)
     _load().oracle_link_gradient(Lv.ctypes.data, bv.ctypes.data, GAMMA.ctypes.data,
                                  x.ctypes.data, lam.ctypes.data, float(kappa), G.ctypes.data)
+    if csw != 0.0:
+        Uc = _c128(U)
+        _load().oracle_clover_gradient(Lv.ctypes.data, GAMMA.ctypes.data, Uc.ctypes.data, x.ctypes.data,
+                                       lam.ctypes.data, float(kappa), float(csw), G.ctypes.data)
     return G
 
 

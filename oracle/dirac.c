@@ -286,3 +286,83 @@ void oracle_link_gradient(const int L[4], const int bc[4], const cplx *gamma,
         }
     }
 }
+
+/* Clover-term part of the link gradient of L = Re<eta, D^{-1} b> (added to G).
+ * With x = D^{-1} b, lam = D^{-dag} eta and F = i kappa c_SW sum_{mu<nu}
+ * sigma_{mu nu} (Q - Q^dag)/8, dL = -Re sum_x lam^dag dF x gives
+ *   dL = (kappa c_SW / 8) sum_x sum_{mu<nu} Im tr[dQ_{mu nu}(x) H_{mu nu}(x)],
+ *   H = W + W^dag,  W = sum_{s,t} sigma_{mu nu}[s][t] x_t(x) lam_s(x)^dag.
+ * For a leaf A1 A2 A3 A4 (each a link or its dagger) the link of A_k enters
+ * through R_k = A_{k+1} .. A4 H A1 .. A_{k-1}: with dL = Re sum conj(G) dU,
+ * G += (kappa c_SW / 8) (i R_k^dag) for an undaggered link and
+ * G += (kappa c_SW / 8) (-i R_k) for a daggered one.  Serial scatter loops. */
+static void m3_mul_to(const cplx *a, const cplx *b, cplx *c) { m3_mul(a, b, c); }
+
+void oracle_clover_gradient(const int L[4], const cplx *gamma, const cplx *U, const cplx *x, const cplx *lam,
+                            double kappa, double csw, cplx *G)
+{
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    const double c = kappa * csw / 8.0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = mu + 1; nu < 4; ++nu) {
+            cplx sigma[16];
+            for (int s = 0; s < 4; ++s)
+                for (int t = 0; t < 4; ++t) {
+                    cplx v = 0.0;
+                    for (int r = 0; r < 4; ++r)
+                        v += gamma[mu * 16 + s * 4 + r] * gamma[nu * 16 + r * 4 + t]
+                           - gamma[nu * 16 + s * 4 + r] * gamma[mu * 16 + r * 4 + t];
+                    sigma[s * 4 + t] = 0.5 * I * v;
+                }
+            for (int64_t s0 = 0; s0 < V; ++s0) {
+                /* W = sum_{s,t} sigma[s][t] x_t lam_s^dag,  H = W + W^dag */
+                cplx W[9], H[9];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        cplx v = 0.0;
+                        for (int s = 0; s < 4; ++s)
+                            for (int t = 0; t < 4; ++t)
+                                v += sigma[s * 4 + t] * x[s0 * 12 + t * 3 + a] * conj(lam[s0 * 12 + s * 3 + b]);
+                        W[a * 3 + b] = v;
+                    }
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) H[a * 3 + b] = W[a * 3 + b] + conj(W[b * 3 + a]);
+                /* the four leaves of Q_{mu nu}(x): links (direction, site, daggered) */
+                int xc[4], y[4];
+                site_coords(L, s0, xc);
+                const int64_t xpm = neighbour(L, xc, mu, +1), xpn = neighbour(L, xc, nu, +1);
+                const int64_t xmm = neighbour(L, xc, mu, -1), xmn = neighbour(L, xc, nu, -1);
+                site_coords(L, xmm, y);
+                const int64_t xmm_pn = neighbour(L, y, nu, +1), xmm_mn = neighbour(L, y, nu, -1);
+                site_coords(L, xmn, y);
+                const int64_t xmn_pm = neighbour(L, y, mu, +1);
+                const int dir[4][4] = {{mu, nu, mu, nu}, {nu, mu, nu, mu}, {mu, nu, mu, nu}, {nu, mu, nu, mu}};
+                const int64_t site[4][4] = {{s0, xpm, xpn, s0}, {s0, xmm_pn, xmm, xmm},
+                                            {xmm, xmm_mn, xmm_mn, xmn}, {xmn, xmn, xmn_pm, s0}};
+                const int dag[4][4] = {{0, 0, 1, 1}, {0, 1, 1, 0}, {1, 1, 0, 0}, {1, 0, 0, 1}};
+                for (int leaf = 0; leaf < 4; ++leaf) {
+                    cplx A[4][9];
+                    for (int k = 0; k < 4; ++k) {
+                        const cplx *u = &U[((int64_t)dir[leaf][k] * V + site[leaf][k]) * 9];
+                        if (dag[leaf][k]) m3_dag(u, A[k]);
+                        else for (int e = 0; e < 9; ++e) A[k][e] = u[e];
+                    }
+                    for (int k = 0; k < 4; ++k) {
+                        /* R = A_{k+1} .. A_4 H A_1 .. A_{k-1} */
+                        cplx R[9], T[9];
+                        for (int e = 0; e < 9; ++e) R[e] = (e % 4 == 0) ? 1.0 : 0.0;
+                        for (int j = k + 1; j < 4; ++j) { m3_mul_to(R, A[j], T); for (int e = 0; e < 9; ++e) R[e] = T[e]; }
+                        m3_mul_to(R, H, T);
+                        for (int e = 0; e < 9; ++e) R[e] = T[e];
+                        for (int j = 0; j < k; ++j) { m3_mul_to(R, A[j], T); for (int e = 0; e < 9; ++e) R[e] = T[e]; }
+                        cplx *g = &G[((int64_t)dir[leaf][k] * V + site[leaf][k]) * 9];
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) {
+                                if (dag[leaf][k]) g[a * 3 + b] += c * (-I) * R[a * 3 + b];
+                                else g[a * 3 + b] += c * I * conj(R[b * 3 + a]);
+                            }
+                    }
+                }
+            }
+        }
+}

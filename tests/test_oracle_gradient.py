@@ -84,3 +84,49 @@ def test_projected_force_fd_full_direction(setup, rng):
     fd = (loss(ex(h) @ U, b, eta) - loss(ex(-h) @ U, b, eta)) / (2 * h)
     an = np.einsum("mvab,mvba->", T, P).real
     assert abs(fd - an) < 1e-6 * abs(an)
+
+
+# --------------------------------------------------------------------------- clover term
+CSW = 1.0
+
+
+@pytest.fixture(scope="module")
+def setup_clover():
+    U = synth.random_links(L, seed=11)
+    b = synth.gaussian_spinor(L, seed=2)
+    eta = synth.gaussian_spinor(L, seed=3)
+    F = oracle.clover_field(U, KAPPA, CSW, L)
+    x = oracle.solve(U, b, KAPPA, L, F=F, tol=TOL)
+    lam = oracle.solve(U, eta, KAPPA, L, F=F, tol=TOL, dagger=True)
+    G = oracle.link_gradient(x, lam, KAPPA, L, U=U, csw=CSW)
+    return U, b, eta, G
+
+
+def loss_clover(U, b, eta):
+    F = oracle.clover_field(U, KAPPA, CSW, L)
+    return np.vdot(eta, oracle.solve(U, b, KAPPA, L, F=F, tol=TOL)).real
+
+
+def test_clover_grad_U_unconstrained_fd(setup_clover, rng):
+    U, b, eta, G = setup_clover
+    E = rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape)
+    h = 1e-5
+    fd = (loss_clover(U + h * E, b, eta) - loss_clover(U - h * E, b, eta)) / (2 * h)
+    an = np.sum(np.conj(G) * E).real
+    assert abs(fd - an) < 1e-6 * abs(an)
+
+
+def test_clover_projected_force_fd(setup_clover, rng):
+    U, b, eta, G = setup_clover
+    P = oracle.projected_force(U, G)
+    h = 1e-5
+    V = oracle.volume(L)
+    for _ in range(8):
+        mu, s = rng.integers(0, 4), rng.integers(0, V)
+        T = _random_su3_algebra(rng)
+        Up, Um = U.copy(), U.copy()
+        Up[mu, s] = expm(1j * h * T) @ U[mu, s]
+        Um[mu, s] = expm(-1j * h * T) @ U[mu, s]
+        fd = (loss_clover(Up, b, eta) - loss_clover(Um, b, eta)) / (2 * h)
+        an = np.trace(T @ P[mu, s]).real
+        assert abs(fd - an) < 1e-6 * max(abs(an), 1e-3), (mu, s, fd, an)
