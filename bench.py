@@ -53,11 +53,13 @@ def parse():
     ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
                     help="solve: the timed mixed-precision solve (default); dslash: the hopping kernel alone")
     ap.add_argument("--workload", default="wilson32",
-                    choices=["wilson32", "prop24", "uneven6", "clover48", "grad16"],
-                    help="wilson32: the default timed solve; prop24: 12 point sources on 24^3x48 in one "
+                    choices=["wilson32", "configs0_8x8x8x8", "prop24", "uneven6", "clover48", "grad16"],
+                    help="wilson32: the default timed solve; configs0_8x8x8x8: plain FP64 dslash + solve on 8^4; prop24: 12 point sources on 24^3x48 in one "
                          "batched solve; uneven6: six lattices of uneven size in one batched solve; "
                          "clover48: Wilson-clover 48^3x96, 4 RHS, FP16 inner, with grad_b; "
                          "grad16: FP64 solve + adjoint + link gradient on 16^3x32")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads that the default line reports under `workloads`")
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "f64df"], help="precision for --mode dslash")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch for --mode dslash")
     return ap.parse_args()
@@ -284,49 +286,61 @@ def run_ours(args, rank, world):
     value = hop_bytes_all / (ms / 1000.0) / 1e9
     true_res = max(s["true_resid"] for s in stats)
 
-    # roofline of the dominant kernel (inner-precision hopping term): one more
-    # solve of the same workload with the host-driven loop, every hopping launch
-    # bracketed by CUDA events on its stream
+    # per-class timing of one more solve of the same workload, host-driven (no
+    # graphs, convergence checked every 4 inner iterations, so a few more
+    # iterations than the timed solve): every kernel launch bracketed by CUDA
+    # events on its stream
     bpp.prof_enable(True)
-    for p in (0, 1, 2, 3):
-        bpp.prof_read(p, reset=True)
+    for c in CLASS_NAMES:
+        bpp.prof_read(c, reset=True)
     bpp.solve(g, b, KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0), x=x)
     torch.cuda.synchronize()
     bpp.prof_enable(False)
-    prof = {p: bpp.prof_read(p, reset=True) for p in (0, 1, 2, 3)}
+    prof = {c: bpp.prof_read(c, reset=False) for c in (0, 1, 2, 3)}
+    peak_hbm, peak_kind = measured_peaks()
+    budget = step_budget(bpp, peak_hbm)
+    alu = _peak_fp64_fp32(dev)
     n_in, ms_in, by_in = prof[inner]
     n64, ms64, by64 = prof[0]
-    peak_hbm, peak_kind = measured_peaks()
+    # the inner-precision hopping kernel: HBM-bound; bytes = 8 links + input and
+    # output spinor per site (392 B for FP16), plus the xpay operand that the
+    # second hop of each Schur application reads (52 B, half of the launches)
     inner_gbs = by_in / (ms_in / 1000.0) / 1e9 if ms_in > 0 else None
     roof_inner = {"bound": "hbm", "achieved": inner_gbs, "peak": peak_hbm, "unit": "GB/s",
                   "frac": (inner_gbs / peak_hbm) if inner_gbs else None, "traffic": None,
                   "kernel": "k_hop inner precision", "peak_kind": peak_kind, "launches": n_in,
-                  "avg_us": 1000 * ms_in / max(n_in, 1), "share_ms": ms_in}
+                  "avg_us": 1000 * ms_in / max(n_in, 1), "share_ms": ms_in,
+                  "bytes_counted": "8 links + in + out spinor per site, + the xpay operand of the second Schur hop"}
     # FP64 hopping kernel: bound by the FP64 pipe; 1320 flop per output site
-    # (the xpay forms add 48, not counted); peak = 148 SMs x 2 FP64 FMA/clk x
-    # 2 flop x max SM clock
     f64_flops = n64 * (V // 2) * 1320.0
-    f64_peak = 148 * 2 * 2 * 2.032e9 / 1e12
     f64_tf = f64_flops / (ms64 / 1000.0) / 1e12 if ms64 > 0 else None
-    roof_f64 = {"bound": "alu", "achieved": f64_tf, "peak": f64_peak, "unit": "TFLOP/s",
-                "frac": (f64_tf / f64_peak) if f64_tf else None, "traffic": None,
-                "kernel": "k_hop FP64 (outer defect correction)", "peak_kind": "derived: 148 SM x 2 DFMA/clk x 2 GHz",
+    roof_f64 = {"bound": "alu", "achieved": f64_tf, "peak": alu["fp64"]["peak"], "unit": "TFLOP/s",
+                "frac": (f64_tf / alu["fp64"]["peak"]) if f64_tf else None, "traffic": None,
+                "kernel": "k_hop FP64 (final true residual)", "peak_kind": alu["fp64"]["peak_kind"],
+                "peak_derived": alu["fp64"]["derived_tflops"], "flop_per_site": 1320,
                 "launches": n64, "avg_us": 1000 * ms64 / max(n64, 1), "share_ms": ms64,
                 "hbm_gbs": (by64 / (ms64 / 1000.0) / 1e9) if ms64 > 0 else None}
+    # double-float hopping kernel: bound by the FP32 pipe; DF_OPS_PER_SITE FP32
+    # operations per output site; peak = FP32 lane operations per second (half
+    # the FMA flop rate)
     nd, msd, byd = prof[3]
-    df_gbs = byd / (msd / 1000.0) / 1e9 if msd > 0 else None
-    roof_df = {"bound": "alu", "achieved": df_gbs, "peak": peak_hbm, "unit": "GB/s",
-               "frac": (df_gbs / peak_hbm) if df_gbs else None, "traffic": None,
-               "kernel": "k_hop double-float (outer defects, FP32 pipe)", "peak_kind": peak_kind,
-               "launches": nd, "avg_us": 1000 * msd / max(nd, 1), "share_ms": msd}
+    df_tops = nd * (V // 2) * DF_OPS_PER_SITE / (msd / 1000.0) / 1e12 if msd > 0 else None
+    df_peak = alu["fp32"]["peak"] / 2.0
+    roof_df = {"bound": "alu", "achieved": df_tops, "peak": df_peak, "unit": "Tops/s (FP32 lane operations)",
+               "frac": (df_tops / df_peak) if df_tops else None, "traffic": None,
+               "kernel": "k_hop double-float (even-odd preparation, outer defects)",
+               "peak_kind": alu["fp32"]["peak_kind"] + ", / 2 (an FMA is 2 flop, 1 operation)",
+               "ops_per_site": DF_OPS_PER_SITE, "launches": nd, "avg_us": 1000 * msd / max(nd, 1), "share_ms": msd,
+               "hbm_gbs": (byd / (msd / 1000.0) / 1e9) if msd > 0 else None}
     # DRAM traffic per launch of the inner hopping kernel, from the committed
-    # ncu capture of this workload (null when the capture does not match)
+    # ncu capture of this workload (a stored figure: null when the capture does
+    # not match this lattice and precision)
     try:
         with open(os.path.join(ROOT, "profiles", "k_hop_f16_32x64_in_solve.json")) as f:
             cap = json.load(f)
         if inner == bpp.F16 and list(L) == cap["lattice"]:
             roof_inner["traffic"] = cap["traffic_bytes_per_launch"]
-            roof_inner["traffic_source"] = "profiles/k_hop_f16_32x64_in_solve.md"
+            roof_inner["traffic_source"] = "stored: profiles/k_hop_f16_32x64_in_solve.md (ncu, not this run)"
     except (OSError, KeyError, ValueError):
         pass
     dominant = max([roof_f64, roof_inner, roof_df], key=lambda r: r["share_ms"])
@@ -387,6 +401,18 @@ def run_ours(args, rank, world):
                "sample": f"FP64 oracle D (Eq. 1, plain C loops, OpenMP) on {sites} random sites of the "
                          f"{L[0]}x{L[1]}x{L[2]}x{L[3]} lattice in {secs:.1f} s; 1536 B per output site"}
 
+    workloads = None
+    if not args.no_workloads and args.lattice is None and world == 1:
+        workloads = {}
+        del g
+        torch.cuda.synchronize()
+        bpp.release_workspace()
+        for name in WORKLOADS:
+            steps = 2 if name == "clover48" else 5
+            workloads[name] = workload_results(name, dev, steps, 1)
+            torch.cuda.synchronize()
+            bpp.release_workspace()
+
     if rank != 0:
         return
     ms_step = ms / args.steps
@@ -415,8 +441,11 @@ def run_ours(args, rank, world):
         "roofline_inner": roof_inner,
         "roofline_fp64": roof_f64,
         "roofline_f64df": roof_df,
-        "roofline_timing": "CUDA events around each hopping launch of one extra host-driven solve of the same workload",
+        "roofline_timing": "CUDA events around each kernel launch of one extra host-driven solve of the same workload",
+        "step_budget": budget,
+        "alu_peaks": alu,
         "cpu_baseline": cpu,
+        "workloads": workloads,
     }
     print(json.dumps(out), flush=True)
 
@@ -478,26 +507,120 @@ def _timed(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps, out
 
 
-def run_workload(args, rank, world):
-    """The batched, clover and gradient workloads (one JSON line each)."""
+def _peak_fp64_fp32(dev):
+    """FP64 and FP32 ALU peaks measured in this run with cuBLAS DGEMM / SGEMM
+    (TF32 off) on 4096^3 (2 N^3 flop, best of 3), beside the peaks derived from
+    the unit counts (148 SMs; 2 FP64 and 128 FP32 FMA lanes per SM and clock)
+    at the maximum SM clock.  A measured figure far above the derived one would
+    mean a library emulation path, and is then not used."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, derived in (("fp64", torch.float64, 148 * 2 * 2 * 2.032e9 / 1e12),
+                                  ("fp32", torch.float32, 148 * 128 * 2 * 2.032e9 / 1e12)):
+            n = 4096
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            tf = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            ok = tf <= 1.15 * derived
+            out[name] = {"measured_tflops": tf, "derived_tflops": derived,
+                         "peak": tf if ok else derived,
+                         "peak_kind": (f"measured: cuBLAS {'D' if name == 'fp64' else 'S'}GEMM 4096^3" if ok
+                                       else "derived from unit counts (the GEMM exceeded it)")}
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
+# Double-float (FP32 hi + lo) operations the even-odd hopping kernel performs
+# per output site, counted from the df64 algorithm as written (df add 8 FP32
+# operations, TwoProd with cross terms 4, lazy accumulation 8, renormalisation
+# 3): per hop 12 df adds (projection) + 12 outputs x (6 products + 5 lazy adds
+# + 1 renormalisation) + 24 df adds (reconstruction) = 1092; 8 hops; + the -kappa
+# scaling (24 df products of 7) and the normalised stores (24 x 3).
+DF_OPS_PER_SITE = 8 * (12 * 8 + 12 * (6 * 4 + 5 * 8 + 3) + 24 * 8) + 24 * 7 + 24 * 3
+
+CLASS_NAMES = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16", 3: "hop_f64df", 4: "krylov_vector",
+               5: "outer_vector", 6: "layout", 7: "control", 8: "clover", 9: "force"}
+
+
+def step_budget(bpp, peak_hbm):
+    """Per kernel class of one profiled solve: launches, ms, share of the GPU
+    time, algorithmic GB/s and its fraction of the HBM peak."""
+    rows, total = {}, 0.0
+    for c, name in CLASS_NAMES.items():
+        n, ms, by = bpp.prof_read(c, reset=True)
+        if n == 0:
+            continue
+        total += ms
+        rows[name] = {"launches": n, "ms": ms, "bytes": by,
+                      "gbs": (by / (ms / 1e3) / 1e9) if (ms > 0 and by > 0) else None}
+    for r in rows.values():
+        r["share"] = r["ms"] / total if total > 0 else None
+        r["frac_hbm"] = (r["gbs"] / peak_hbm) if r["gbs"] else None
+    return {"classes": rows, "gpu_ms": total}
+
+
+def workload_results(name, dev, steps, warm):
+    """One of the other workloads (batched, clover, gradient, plain FP64), timed
+    with CUDA events on the current stream: ms per step, algorithmic GB/s of the
+    hopping kernels, true residuals, and the oracle's CPU time where it is
+    feasible."""
     import numpy as np
     import torch
 
     import paper_2111_04457_b300 as bpp
     import synth
     from paper_2111_04457_b300.autograd import solve_fn
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    steps, warm = args.steps, max(args.warmup, 1)
-    out = {"metric": METRIC, "unit": "GB/s", "n_gpus": world, "steps": steps, "warmup": warm,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    out = {}
 
     def work_bytes(reset=True):
         return sum(bpp.work_read(p, reset=reset)[1] for p in (0, 1, 2, 3))
 
-    if args.workload == "prop24":
+    if name == "configs0_8x8x8x8":
+        L = (8, 8, 8, 8)
+        U_np = synth.random_links(L, seed=1)
+        b_np = synth.gaussian_spinor(L, seed=2)
+        g = bpp.Gauge(torch.from_numpy(U_np).to(dev), L)
+        b = torch.from_numpy(b_np).to(dev)
+        V = L[0] * L[1] * L[2] * L[3]
+        par = (np.indices(L[::-1]).sum(axis=0).ravel()) & 1        # parity of lexicographic sites
+        be, bo = b[torch.from_numpy(np.flatnonzero(par == 0)).to(dev)], b[torch.from_numpy(np.flatnonzero(par == 1)).to(dev)]
+        ms_d, out_e = _timed(lambda: bpp.dslash(g, bo, KAPPA, bpp.EVEN, bpp.F64), 50, 5, stream)
+        # bhat = b_e - D_eo b_o = b_e - (-kappa H_eo b_o); the library stops on the
+        # full-D residual = Schur residual x ||bhat|| / ||b||
+        bhat_n = torch.linalg.vector_norm(be - out_e).item()
+        tol = 1e-12 * bhat_n / torch.linalg.vector_norm(b).item()
+        o = bpp.solve_opts(inner_prec=bpp.F64)
+        work_bytes()
+        ms, st = _timed(lambda: bpp.solve(g, b, KAPPA, 0.0, tol, o)[1], steps, warm, stream)
+        by = work_bytes() / (steps + warm)
+        import oracle
+        t0 = time.perf_counter()
+        oracle.solve(U_np, b_np, KAPPA, L, tol=1e-12)
+        cpu_s = time.perf_counter() - t0
+        out = {"workload": "plain FP64 on 8^4: one dslash, then FP64 even-odd BiCGStab to Schur residual 1e-12",
+               "dslash_ms": ms_d, "dslash_gbs": (V // 2) * BYTES_F64 / (ms_d / 1e3) / 1e9,
+               "dslash_note": "8^4 fits in L2: an L2 figure, not an HBM one",
+               "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "true_resid": st[0]["true_resid"],
+               "schur_resid_target": 1e-12, "inner_iters": st[0]["inner_iters"],
+               "oracle_solve_s": cpu_s, "oracle_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+    elif name == "prop24":
         L = (24, 24, 24, 48)
         g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
         b = torch.from_numpy(np.stack([synth.point_source(L, i) for i in range(12)])).to(dev)
@@ -508,12 +631,12 @@ def run_workload(args, rank, world):
         by = work_bytes() / (steps + warm)
         xs = torch.empty_like(b[0])
         ms1, _ = _timed(lambda: [bpp.solve(g, b[i], KAPPA, 0.0, TOL, o, x=xs) for i in range(12)], 1, 1, stream)
-        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f32 inner, f64 outer",
-                   config={"workload": "12 spin-colour point sources on 24^3x48, one batched solve (FP32 inner, "
-                                       "FP64-class outer) to true resid 1e-10", "lattice": list(L), "rhs": 12},
-                   ms_per_rhs=ms / 12, ms_12_sequential_single_rhs=ms1, batching_speedup=ms1 / ms,
-                   true_resid_max=max(s["true_resid"] for s in st))
-    elif args.workload == "uneven6":
+        out = {"workload": "12 spin-colour point sources on 24^3x48, one batched solve (FP32 inner, FP64 outer) "
+                           "to true resid 1e-10",
+               "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "ms_per_rhs": ms / 12,
+               "ms_12_sequential_single_rhs": ms1, "batching_speedup": ms1 / ms,
+               "true_resid_max": max(s["true_resid"] for s in st)}
+    elif name == "uneven6":
         lats = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (20, 20, 20, 40), (24, 24, 24, 48)]
         kap = synth.uniform_kappas(len(lats), seed=4)
         gs = [bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L) for L in lats]
@@ -525,11 +648,11 @@ def run_workload(args, rank, world):
         by = work_bytes() / (steps + warm)
         ms1, _ = _timed(lambda: [bpp.solve(gs[i], bs[i], kap[i], 0.0, TOL, o, x=xs[i]) for i in range(6)], 1, 1,
                         stream)
-        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f32 inner, f64 outer",
-                   config={"workload": "6 lattices 8^4 12^4 16^4 16^3x32 20^3x40 24^3x48 (1204992 sites), kappa "
-                                       "U[0.10,0.12], one batched solve", "lattices": [list(L) for L in lats]},
-                   ms_6_sequential=ms1, batching_speedup=ms1 / ms, true_resid_max=max(s["true_resid"] for s in st))
-    elif args.workload == "clover48":
+        out = {"workload": "6 lattices 8^4 12^4 16^4 16^3x32 20^3x40 24^3x48 (1204992 sites), kappa U[0.10,0.12], "
+                           "one batched solve (FP32 inner, FP64 outer) to true resid 1e-10",
+               "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "ms_6_sequential": ms1, "batching_speedup": ms1 / ms,
+               "true_resid_max": max(s["true_resid"] for s in st)}
+    elif name == "clover48":
         L = (48, 48, 48, 96)
         csw = 1.0
         g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
@@ -545,22 +668,26 @@ def run_workload(args, rank, world):
             bb = b.clone().requires_grad_(True)
             xx = solve_fn(None, bb, L, KAPPA, csw=csw, tol=TOL, inner_prec=bpp.F16, gauge=g)
             torch.vdot(eta.reshape(-1), xx.reshape(-1)).real.backward()
-            return bb.grad
+            return xx.detach(), bb.grad
         work_bytes()
-        ms, lam = _timed(step, steps, warm, stream)
+        ms, (xx, lam) = _timed(step, steps, warm, stream)
         by = work_bytes() / (steps + warm)
-        Dl = bpp.dirac_apply(g, lam[0], KAPPA, csw, dagger=True)
-        res = (torch.linalg.vector_norm(eta[0] - Dl) / torch.linalg.vector_norm(eta[0])).item()
-        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f16-storage/f32 inner, f64 outer",
-                   config={"workload": "Wilson-clover c_SW=1 48^3x96, 4 Gaussian RHS: forward solve + adjoint "
-                                       "solve for grad_b (FP16 inner, FP64-class outer, true resid 1e-10)",
-                           "lattice": list(L), "rhs": 4, "csw": csw},
-                   clover_build_ms=build_ms, adjoint_true_resid_rhs0=res)
-    elif args.workload == "grad16":
+        res_x = max((torch.linalg.vector_norm(b[r] - bpp.dirac_apply(g, xx[r], KAPPA, csw)) /
+                     torch.linalg.vector_norm(b[r])).item() for r in range(4))
+        res_l = max((torch.linalg.vector_norm(eta[r] - bpp.dirac_apply(g, lam[r], KAPPA, csw, dagger=True)) /
+                     torch.linalg.vector_norm(eta[r])).item() for r in range(4))
+        out = {"workload": "Wilson-clover c_SW=1 48^3x96, 4 Gaussian RHS: forward solve + adjoint solve for grad_b "
+                           "(FP16-storage inner, FP64 outer, true resid 1e-10)",
+               "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "clover_build_ms": build_ms,
+               "true_resid_max": res_x, "adjoint_true_resid_max": res_l}
+        del g, b, eta, xx, lam
+    elif name == "grad16":
         L = (16, 16, 16, 32)
-        U = torch.from_numpy(synth.random_links(L, seed=1)).to(dev)
-        b = torch.from_numpy(synth.gaussian_spinor(L, seed=2)).to(dev)
-        eta = torch.from_numpy(synth.gaussian_spinor(L, seed=3)).to(dev)
+        U_np = synth.random_links(L, seed=1)
+        b_np, eta_np = synth.gaussian_spinor(L, seed=2), synth.gaussian_spinor(L, seed=3)
+        U = torch.from_numpy(U_np).to(dev)
+        b = torch.from_numpy(b_np).to(dev)
+        eta = torch.from_numpy(eta_np).to(dev)
         g = bpp.Gauge(U, L)
 
         def step():
@@ -572,11 +699,37 @@ def run_workload(args, rank, world):
         work_bytes()
         ms, gU = _timed(step, steps, warm, stream)
         by = work_bytes() / (steps + warm)
-        out.update(value=by / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f64",
-                   config={"workload": "L = Re<eta, D^-1 b> on 16^3x32 FP64: forward solve, adjoint solve, "
-                                       "recomputed x, link-gradient kernel", "lattice": list(L)})
+        import oracle
+        t0 = time.perf_counter()
+        x_o = oracle.solve(U_np, b_np, KAPPA, L, tol=1e-12)
+        lam_o = oracle.solve(U_np, eta_np, KAPPA, L, tol=1e-12, dagger=True)
+        G_o = oracle.link_gradient(x_o, lam_o, KAPPA, L)
+        cpu_s = time.perf_counter() - t0
+        err = float(np.linalg.norm(gU.cpu().numpy() - G_o) / np.linalg.norm(G_o))
+        out = {"workload": "L = Re<eta, D^-1 b> on 16^3x32 FP64: forward solve, adjoint solve, recomputed x, "
+                           "link-gradient kernel",
+               "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "grad_U_rel_err_vs_oracle": err,
+               "oracle_s": cpu_s, "oracle_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+    torch.cuda.synchronize()
+    out["steps"], out["warmup"] = steps, warm
+    return out
+
+
+WORKLOADS = ["configs0_8x8x8x8", "prop24", "uneven6", "grad16", "clover48"]
+
+
+def run_workload(args, rank, world):
+    """One of the other workloads as its own JSON line."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    r = workload_results(args.workload, dev, args.steps, max(args.warmup, 1))
     if rank == 0:
-        print(json.dumps(out), flush=True)
+        print(json.dumps({"metric": METRIC, "value": r["gbs"], "unit": "GB/s", "n_gpus": world, "steps": r["steps"],
+                          "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+                          "config": {"workload": r["workload"]}, "result": r}), flush=True)
 
 
 def main():

@@ -129,17 +129,21 @@ int bpp_dslash(bpp_gauge U, const void* psi, void* out, double kappa, int parity
  * allocation failing or stalling partway through).  No counterpart in the
  * paper: it is the same hopping term as bpp_dslash, with the call's working
  * storage (the system table and the two internal half fields) taken from one
- * file-scope device array of 32 MiB that every GPU loading the library holds
- * until exit, instead of being allocated.  Arguments, layouts and results are
+ * file-scope device array of 32 MiB, placed on a GPU when the first gauge field
+ * is created there and held until the process exits, instead of being
+ * allocated.  Arguments, layouts and results are
  * those of bpp_dslash with parity BPP_EVEN or BPP_ODD (BPP_FULL is rejected).
  * Needs 256-byte-rounded 64 system descriptors plus 2 * nrhs half fields of
  * (Vh rounded up to 64) * {192, 96, 52} bytes for F64/F32/F16; larger requests
  * return BPP_ERR_INVALID_ARG with the sizes in the message.  The current device
- * must be the gauge field's device.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) and should come before
- * any stream capture.  All calls share the one array: calls that can overlap
- * on the GPU (different streams without ordering between them) race and give
- * wrong results; calls on one stream are ordered and safe.  Calls no
+ * must be the gauge field's device.  The array's device address is looked up
+ * (cudaGetSymbolAddress, which also places the array on the device under lazy
+ * module loading) when a gauge field is created on that device, so this call
+ * itself finds it in place.  The system table is written by a kernel from a
+ * descriptor passed by value: no host buffer is read after the call returns.
+ * All calls share the one array: calls that can overlap on the GPU (different
+ * streams without ordering between them) race and give wrong results; calls
+ * on one stream are ordered and safe.  Calls no
  * cudaMalloc, cudaFree or other allocating routine. */
 int bpp_dslash_noalloc(bpp_gauge U, const void* psi, void* out, double kappa, int parity, int prec,
                        int nrhs, bpp_stream stream);
@@ -238,29 +242,48 @@ int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* co
                     const double* kappa, double csw, double tol, const bpp_solve_opts* opts,
                     bpp_solve_stats* stats, bpp_stream stream);
 
-/* Link gradient of L = Re<eta, D^{-1} b> for the Wilson hopping term, given
- * x = D^{-1} b and lam = D^{-dag} eta (complex128 [V][4][3], device):
- *   G_mu(x) = kappa * bc * M_mu(x)^dag,
- *   M_mu(x) = sum_spin [ x(x+mu) ((1 - gamma_mu) lam(x))^dag + ((1 + gamma_mu) lam(x+mu)) x(x)^dag ]
- * (dL = -Re<lam, dD x> with dD read off Eq. (1)).  With project_su3 != 0 the
- * output is instead the traceless Hermitian force
+/* Link gradient of L = Re<eta, D^{-1} b> (the fermion force of the HMC use of
+ * the solve, Sec. 2) for the matrix of Eq. (1), given x = D^{-1} b and
+ * lam = D^{-dag} eta for nrhs right-hand sides (complex128 [nrhs][V][4][3],
+ * device), summed over the right-hand sides.  From dL = -Re<lam, dD x>,
+ * written dL = Re sum conj(G) dU:
+ *   hopping term:  G_mu(x) = kappa * bc * M_mu(x)^dag,
+ *     M_mu(x) = sum_spin [ x(x+mu) ((1 - gamma_mu) lam(x))^dag + ((1 + gamma_mu) lam(x+mu)) x(x)^dag ];
+ *   clover term (csw != 0; the links of its four-plaquette leaves, no
+ *   boundary signs):  dL = (kappa c_SW / 8) sum_x sum_{mu<nu} Im tr[dQ_{mu nu}(x) H_{mu nu}(x)],
+ *     H = W + W^dag, W = sum_{s,t} sigma_{mu nu}[s][t] x_t(x) lam_s(x)^dag,
+ *     so a link in leaf position k adds (kappa c_SW / 8) i R_k^dag (or
+ *     -(kappa c_SW / 8) i R_k where the leaf holds its dagger), R_k the leaf
+ *     product cycled to start after the link, with H inserted at the leaf's
+ *     base site.
+ * With project_su3 != 0 the output is instead the traceless Hermitian force
  *   P_mu(x) = (i/2)(U G^dag - G U^dag) - trace/3,  so that dL/deps = tr(T P)
- * for U_mu(x) -> exp(i eps T) U_mu(x).
- * dU: complex128 [4][V][3][3], device, caller-owned.
- * Errors: INVALID_ARG, OOM, CUDA. */
-int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, void* dU, int project_su3,
-              bpp_stream stream);
+ * for U_mu(x) -> exp(i eps T) U_mu(x).  The clover part needs no
+ * bpp_clover_build (it uses the links only).
+ * dU: complex128 [4][V][3][3], device, caller-owned, overwritten.
+ * Errors: INVALID_ARG (NULL or host pointer, nrhs outside 1..64, non-finite
+ * kappa or csw), OOM (the clover part's 864 B per site of scratch), CUDA. */
+int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, double csw, int nrhs, void* dU,
+              int project_su3, bpp_stream stream);
 
 /* Number of kernels this library has launched since load (or since the last
  * reset when reset != 0); graph launches count each kernel node they run. */
 int64_t bpp_launch_count(int reset);
 
-/* Kernel timing: while enabled, every launch of the even-odd hopping kernels
- * outside a CUDA graph is bracketed by CUDA events on its stream. */
+/* Kernel timing: while enabled, every kernel launch of the library outside a
+ * CUDA graph is bracketed by CUDA events on its stream and credited to its
+ * kernel class. */
 int bpp_prof_enable(int enable);
-/* Reads (and with reset != 0 clears) the accumulated hopping-kernel timings for
- * precision prec: number of launches, total milliseconds, total algorithmic
- * bytes.  Synchronises the device. */
+/* Reads (and with reset != 0 clears) the accumulated timings of kernel class
+ * `prec`: number of launches, total milliseconds, total algorithmic bytes
+ * (each operand and result counted once per launch).  Classes: 0..3 the
+ * even-odd hopping kernels in BPP_F64 / BPP_F32 / BPP_F16 / BPP_F64DF (bytes:
+ * 8 links + input + output spinor per site, + fused operands); 4 the Krylov
+ * vector kernels (fused updates and reductions); 5 the outer defect-
+ * correction vector kernels (residuals, down-conversion, accumulation);
+ * 6 the boundary layout conversion; 7 the single-warp control kernels (no
+ * bytes); 8 the clover apply (and build, no bytes); 9 the force kernel.
+ * Synchronises the device.  Errors: INVALID_ARG (class out of range). */
 int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int reset);
 
 /* Reads (and with reset != 0 clears) the work done by the even-odd hopping

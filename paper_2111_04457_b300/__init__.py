@@ -81,7 +81,7 @@ _SIGS = {
     "bpp_solve": ([_p, _p, _p, _d, _d, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_solve_batch": ([_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_d), _d, _d,
                          ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
-    "bpp_force": ([_p, _p, _p, _d, _p, _i, _p], _i),
+    "bpp_force": ([_p, _p, _p, _d, _d, _i, _p, _i, _p], _i),
     "bpp_launch_count": ([_i], _i64),
     "bpp_prof_enable": ([_i], _i),
     "bpp_prof_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), ctypes.POINTER(_d), _i], _i),
@@ -228,8 +228,11 @@ def dslash(g: Gauge, psi: torch.Tensor, kappa: float, parity: int, prec: int = F
 def dslash_noalloc(g: Gauge, psi: torch.Tensor, kappa: float, parity: int, prec: int = F64, out=None, stream=None):
     """The EVEN/ODD hopping term of dslash() without any device allocation by
     the library: for callers whose device memory is owned by another manager.
-    The library's working storage is a fixed 32 MiB device array (requests that
-    need more raise BppError); concurrent calls on unordered streams race."""
+    The library's working storage is a fixed 32 MiB device array, placed on the
+    device when the gauge field was created (requests that need more raise
+    BppError); concurrent calls on unordered streams race.  out, if given, must
+    be a contiguous CUDA tensor of psi's dtype, size and device that does not
+    overlap psi (ValueError otherwise)."""
     _cuda(psi, "psi")
     if psi.dtype != _cdtype(prec):
         raise ValueError(f"psi must be {_cdtype(prec)} for precision {prec}")
@@ -237,6 +240,20 @@ def dslash_noalloc(g: Gauge, psi: torch.Tensor, kappa: float, parity: int, prec:
     psi = psi.contiguous()
     if out is None:
         out = torch.empty_like(psi)
+    else:
+        # the library writes n * Vh * 12 elements of complex<prec> through out
+        if out.dtype != psi.dtype:
+            raise ValueError(f"out must be {psi.dtype} for precision {prec}")
+        if out.numel() != psi.numel():
+            raise ValueError("out must have as many elements as psi")
+        if not out.is_cuda or out.device != psi.device:
+            raise ValueError("out must be a CUDA tensor on psi's device")
+        if not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        o0, o1 = out.data_ptr(), out.data_ptr() + out.numel() * out.element_size()
+        p0, p1 = psi.data_ptr(), psi.data_ptr() + psi.numel() * psi.element_size()
+        if o0 < p1 and p0 < o1:
+            raise ValueError("out must not overlap psi")
     _check(_lib.bpp_dslash_noalloc(g.handle, _ptr(psi), _ptr(out), float(kappa), parity, prec, n, _stream(stream)))
     return out
 
@@ -345,14 +362,23 @@ def solve_batch(gauges, bs, kappas, tol: float = 1e-10, opts: SolveOpts = None, 
     return xs, stats
 
 
-def force(g: Gauge, x: torch.Tensor, lam: torch.Tensor, kappa: float, project: bool = False, stream=None):
+def force(g: Gauge, x: torch.Tensor, lam: torch.Tensor, kappa: float, project: bool = False, csw: float = 0.0,
+          stream=None):
     """Link gradient G (project=False) or projected force P (project=True) of
-    L = Re<eta, D^-1 b>, given x = D^-1 b and lam = D^-dag eta (complex128 [V][4][3])."""
+    L = Re<eta, D^-1 b>, given x = D^-1 b and lam = D^-dag eta (complex128
+    [V][4][3] or [nrhs][V][4][3], summed over the right-hand sides); csw != 0
+    adds the clover term's part."""
     _cuda(x, "x")
     _cuda(lam, "lam")
+    if x.dtype != torch.complex128 or lam.dtype != torch.complex128:
+        raise ValueError("x and lam must be complex128")
+    if x.shape != lam.shape:
+        raise ValueError("x and lam must have the same shape")
     x, lam = x.contiguous(), lam.contiguous()
+    n = _nrhs(x, 12 * g.lattice.V)
     out = torch.empty((4, g.lattice.V, 3, 3), dtype=torch.complex128, device=x.device)
-    _check(_lib.bpp_force(g.handle, _ptr(x), _ptr(lam), float(kappa), _ptr(out), int(project), _stream(stream)))
+    _check(_lib.bpp_force(g.handle, _ptr(x), _ptr(lam), float(kappa), float(csw), n, _ptr(out), int(project),
+                          _stream(stream)))
     return out
 
 

@@ -9,7 +9,8 @@ Backward, for a real loss L with incoming gradient eta = dL/dRe x + i dL/dIm x
            (the fermion-force kernel), from dL = -Re<lam, dD x>.
 x is not kept from the forward Krylov iterations: with recompute=True (default)
 backward re-solves it in mixed precision from b; otherwise the forward x is saved.
-The link gradient covers the Wilson hopping term; csw != 0 supports grad_b only.
+With csw != 0 the link gradient includes the clover term's part (the
+derivative of the four-plaquette leaves of F).
 """
 from __future__ import annotations
 
@@ -41,23 +42,19 @@ class SolveFn(torch.autograd.Function):
         grad_b = lam[0] if ctx.single else lam
         grad_U = None
         if ctx.needs_input_grad[0]:
-            if ctx.csw != 0.0:
-                raise NotImplementedError("link gradient of the clover term is not implemented (grad_b is)")
             (saved,) = ctx.saved_tensors
             if ctx.recompute:
                 x, _ = solve(g, saved, ctx.kappa, ctx.csw, ctx.tol, solve_opts(inner_prec=ctx.inner_prec))
             else:
                 x = saved
-            grad_U = None
-            for r in range(x.shape[0]):
-                G = force(g, x[r], lam[r], ctx.kappa, project=False)
-                grad_U = G if grad_U is None else grad_U + G
+            # summed over the right-hand sides by the force kernel
+            grad_U = force(g, x, lam, ctx.kappa, project=False, csw=ctx.csw)
         return grad_U, grad_b, None, None, None, None, None, None
 
 
 def solve_fn(U: torch.Tensor, b: torch.Tensor, L, kappa: float, csw: float = 0.0, tol: float = 1e-10,
              inner_prec: int = F32, gauge: Gauge = None, bc=(1, 1, 1, -1), recompute: bool = True):
-    """x = D[U]^{-1} b with gradients for b and (Wilson) U.
+    """x = D[U]^{-1} b with gradients for b and U (Wilson or Wilson-clover).
 
     U: complex128 [4][V][3][3] CUDA tensor; b: complex128 [V][4][3] or [nrhs][V][4][3].
     gauge: optional prebuilt Gauge for U (with its clover term if csw != 0)."""

@@ -16,6 +16,7 @@ int prof_read(int prec, int64_t* n, double* ms, double* bytes, int reset);
 int64_t launch_count(int reset);
 int work_read(int prec, int64_t* n, double* bytes, int reset);
 int release_workspace();
+int noalloc_prepare(int dev, cudaStream_t st, std::string* err, void** ptr);
 }  // namespace bpp
 
 using namespace bpp;
@@ -110,6 +111,13 @@ int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream strea
             G->Vh = V / 2;
             G->stride = pad_stride(G->Vh);
             BPP_CUDA(cudaGetDevice(&G->device));
+            // places the fixed scratch array of bpp_dslash_noalloc on this
+            // device now, so that entry point never causes an allocation
+            {
+                std::string err;
+                const int rc = noalloc_prepare(G->device, st, &err, nullptr);
+                BPP_REQUIRE(rc == BPP_OK, rc, err);
+            }
             for (int p = 0; p < NPREC; ++p) BPP_CUDA(cudaMalloc(&G->links[p], 8 * link_alloc_bytes(p, G->stride)));
             const size_t bytes = (size_t)V * 4 * 9 * 16;
             if (is_device_ptr(U_lex)) {
@@ -330,12 +338,16 @@ int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* co
     });
 }
 
-int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, void* dU, int project_su3,
-              bpp_stream stream) {
+int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, double csw, int nrhs, void* dU,
+              int project_su3, bpp_stream stream) {
     return guard("bpp_force", [&]() -> int {
         check_gauge(U);
         BPP_REQUIRE(x && lam && dU, BPP_ERR_INVALID_ARG, "NULL field");
-        force(*U, x, lam, kappa, dU, project_su3 ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
+        BPP_REQUIRE(nrhs >= 1 && nrhs <= MAXSYS, BPP_ERR_INVALID_ARG, "nrhs must be 1..64");
+        BPP_REQUIRE(std::isfinite(kappa) && std::isfinite(csw), BPP_ERR_INVALID_ARG, "kappa and csw must be finite");
+        BPP_REQUIRE(is_device_ptr(x) && is_device_ptr(lam) && is_device_ptr(dU), BPP_ERR_INVALID_ARG,
+                    "x, lam and dU must be device memory");
+        force(*U, x, lam, kappa, csw, nrhs, dU, project_su3 ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
         return BPP_OK;
     });
 }

@@ -258,6 +258,9 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
     bp.sc = sc;
     bp.partials = rb.partials.as<double>();
     bp.tickets = rb.tickets.as<unsigned>();
+    // vectors each op reads plus writes (its algorithmic traffic per site)
+    static const int passes[] = {5, 2, 3, 2, 7, 4, 3, 2, 1, 6, 4, 1, 2};
+    ProfScope prof(PROF_BLAS, bt.sites() * spinor_bytes(P) * passes[op], st);
     switch (op) {
         case B_INIT_BICG: k_blas<P, B_INIT_BICG><<<nb, BLAS_B, 0, st>>>(bp); break;
         case B_ALPHA: k_blas<P, B_ALPHA><<<nb, BLAS_B, 0, st>>>(bp); break;
@@ -447,6 +450,7 @@ void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st) 
     op.b = x64;
     op.c = nullptr;
     op.sc = nullptr;
+    ProfScope prof(PROF_OUTER, b64.sites() * 384.0, st);
     k_split_to_f64<<<nb, BLAS_B, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -480,6 +484,7 @@ void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaS
     op.b = out;
     op.c = nullptr;
     op.sc = nullptr;
+    ProfScope prof(PROF_OUTER, b32.sites() * (96.0 + spinor_bytes(bin.prec)), st);
     if (bin.prec == P16) k_to_f32<P16><<<nb, BLAS_B, 0, st>>>(op);
     else if (bin.prec == P32) k_to_f32<P32><<<nb, BLAS_B, 0, st>>>(op);
     else throw Error(BPP_ERR_UNSUPPORTED, "to_f32 takes FP16 or FP32 vectors");
@@ -534,6 +539,7 @@ void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m3
     op.sc = sc;
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
+    ProfScope prof(PROF_OUTER, b64.sites() * (2 * 192.0 + 96.0), st);
     k_defect_update<<<nb, BLAS_B, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -590,7 +596,8 @@ __global__ void __launch_bounds__(BLAS_B) k_f64_to_split(OuterParams op) {
     Access<P64S>::store_spinor(sys_view<P64S>(op.b, d), i, w);
 }
 
-static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, char* b, KScal* sc, cudaStream_t st) {
+static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, char* b, KScal* sc, double bytes,
+                         cudaStream_t st) {
     OuterParams op;
     op.s64 = b64.dev();
     op.sP = b64.dev();
@@ -600,19 +607,22 @@ static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, c
     op.b = b;
     op.c = nullptr;
     op.sc = sc;
+    ProfScope prof(PROF_OUTER, bytes, st);
     kern<<<nb, BLAS_B, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
 
-void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) { launch_outer(k_scale_f64, b64, v, nullptr, sc, st); }
+void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) {
+    launch_outer(k_scale_f64, b64, v, nullptr, sc, b64.sites() * 384.0, st);
+}
 
 void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st) {
-    launch_outer(k_scale_split, b64, v, out, sc, st);
+    launch_outer(k_scale_split, b64, v, out, sc, b64.sites() * (out ? 576.0 : 384.0), st);
 }
 
 void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st) {
-    launch_outer(k_f64_to_split, b64, const_cast<char*>(in), out, nullptr, st);
+    launch_outer(k_f64_to_split, b64, const_cast<char*>(in), out, nullptr, b64.sites() * 384.0, st);
 }
 
 // Odd half of the final check, all FP64: with h = kappa H_oe x_e (op.b) and
@@ -663,6 +673,7 @@ void odd_reconstruct(const Batch& b64, bool clover, const char* bo, const char* 
     op.sc = sc;
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
+    ProfScope prof(PROF_OUTER, b64.sites() * (3 * 192.0 + (clover ? 2 * 576.0 : 0.0)), st);
     if (clover) k_odd_reconstruct<true><<<nb, BLAS_B, 0, st>>>(op);
     else k_odd_reconstruct<false><<<nb, BLAS_B, 0, st>>>(op);
     count_launch();
@@ -682,6 +693,7 @@ void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal*
     op.sc = sc;
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
+    ProfScope prof(PROF_OUTER, b64.sites() * (m_s ? 3 : 2) * 192.0, st);
     k_split_residual<<<nb, BLAS_B, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -700,6 +712,7 @@ void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& 
     op.sc = sc;
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
+    ProfScope prof(PROF_OUTER, b64.sites() * 3 * 192.0, st);
     k_outer_residual<<<nb, BLAS_B, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -716,6 +729,7 @@ void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo
     op.b = lo;
     op.c = nullptr;
     op.sc = const_cast<KScal*>(sc);
+    ProfScope prof(PROF_OUTER, b64.sites() * (192.0 + spinor_bytes(bP.prec)), st);
     if (split) {
         if (bP.prec == P64) k_outer_down<P64, true><<<nb, BLAS_B, 0, st>>>(op);
         else if (bP.prec == P32) k_outer_down<P32, true><<<nb, BLAS_B, 0, st>>>(op);
@@ -740,6 +754,7 @@ void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* 
     op.b = const_cast<char*>(e);
     op.c = x_split;
     op.sc = const_cast<KScal*>(sc);
+    ProfScope prof(PROF_OUTER, b64.sites() * (2 * 192.0 + spinor_bytes(bP.prec) + (x_split ? 2 * 192.0 : 0.0)), st);
     if (bP.prec == P64) k_outer_acc<P64><<<nb, BLAS_B, 0, st>>>(op);
     else if (bP.prec == P32) k_outer_acc<P32><<<nb, BLAS_B, 0, st>>>(op);
     else k_outer_acc<P16><<<nb, BLAS_B, 0, st>>>(op);

@@ -59,6 +59,11 @@ struct Error : public std::runtime_error {
 enum Prec { P64 = BPP_F64, P32 = BPP_F32, P16 = BPP_F16, P64S = 3 };
 constexpr int NPREC = 4;
 
+// Kernel classes of the launch timing (bpp_prof_read): the hopping kernels
+// per precision (0..3 = Prec), then the other kernel families.
+enum ProfClass { PROF_BLAS = 4, PROF_OUTER = 5, PROF_LAYOUT = 6, PROF_CTL = 7, PROF_CLOVER = 8, PROF_FORCE = 9 };
+constexpr int NPROF = 10;
+
 template <int P> struct PT;
 template <> struct PT<P64> {
     using real = double;
@@ -401,7 +406,10 @@ bool capturing(cudaStream_t s);
 // function of its inputs (it is launched several times).
 int tune_lookup(const std::string& key);
 void tune_store(const std::string& key, int block);
-// Hopping-kernel timing (bpp_prof_enable / bpp_prof_read).
+// Launch timing (bpp_prof_enable / bpp_prof_read): while enabled, a
+// ProfScope brackets the launches made in its lifetime with CUDA events on
+// its stream and credits them to kernel class `prec` (a Prec for the hopping
+// kernels, else a ProfClass) with `bytes` of algorithmic traffic.
 struct ProfScope {
     int prec;
     double bytes;

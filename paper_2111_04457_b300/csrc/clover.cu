@@ -233,6 +233,7 @@ void clover_build(Gauge& G, double kappa, double csw, cudaStream_t st) {
     BPP_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
     cp.bad = bad.as<int>();
     const int B = 128;
+    ProfScope prof(PROF_CLOVER, 0.0, st);
     k_clover_build<<<(unsigned)((2 * G.Vh + B - 1) / B), B, 0, st>>>(cp);
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -260,12 +261,15 @@ __global__ void k_clover_apply(const SysDesc* sys, int parity, int inverse, char
     Access<P>::store_spinor(sys_view<P>(out, d), i, w);
 }
 
+static double PTC_bytes(int prec) { return (prec == P64 || prec == P64S) ? 576.0 : prec == P32 ? 288.0 : 144.0; }
+
 void clover_apply(const Batch& b, int parity, int inverse, char* in, char* out, cudaStream_t st) {
     for (auto& s : b.sys)
         BPP_REQUIRE((inverse ? s.Ainv[parity].data : s.A[parity].data) != nullptr, BPP_ERR_UNSUPPORTED,
                     "clover term not built (call bpp_clover_build)");
     const int B = 256;
     dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
+    ProfScope prof(PROF_CLOVER, b.sites() * (2.0 * spinor_bytes(b.prec) + PTC_bytes(b.prec)), st);
     if (b.prec == P64) k_clover_apply<P64><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
     else if (b.prec == P32) k_clover_apply<P32><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);
     else if (b.prec == P16) k_clover_apply<P16><<<grid, B, 0, st>>>(b.dev(), parity, inverse, in, out);

@@ -54,6 +54,12 @@ struct Batch {
     }
     const SysDesc* dev() const { return dsys.as<SysDesc>(); }
     int nsys() const { return (int)sys.size(); }
+    // half-lattice sites of all systems
+    double sites() const {
+        double n = 0;
+        for (auto& d : sys) n += d.g.Vh;
+        return n;
+    }
 };
 
 // Appends one system on gauge G (kappa, clover if csw != 0) to batch b.

@@ -116,6 +116,7 @@ void full_to_eo(const Batch& b, int sys0, int nsys, const void* canon, int canon
                 char* even, char* odd, int g5, cudaStream_t st) {
     const int B = 256;
     dim3 grid((unsigned)((2 * (int64_t)b.Vh_max + B - 1) / B), nsys);
+    ProfScope prof(PROF_LAYOUT, 2.0 * b.sys[sys0].g.Vh * nsys * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
         if (canon_f64)
             k_full_to_eo<PP, double2><<<grid, B, 0, st>>>(b.dev(), sys0, static_cast<const double2*>(canon), cstride, even, odd, g5);
@@ -130,6 +131,7 @@ void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char
                 int64_t cstride, int g5, cudaStream_t st, double scale) {
     const int B = 256;
     dim3 grid((unsigned)((2 * (int64_t)b.Vh_max + B - 1) / B), nsys);
+    ProfScope prof(PROF_LAYOUT, 2.0 * b.sys[sys0].g.Vh * nsys * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
         if (canon_f64)
             k_eo_to_full<PP, double2><<<grid, B, 0, st>>>(b.dev(), sys0, even, odd, static_cast<double2*>(canon), cstride, g5, scale);
@@ -143,6 +145,7 @@ void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char
 void half_to_int(const Batch& b, const void* canon, int canon_f64, char* out, cudaStream_t st) {
     const int B = 256;
     dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
+    ProfScope prof(PROF_LAYOUT, b.sites() * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
         if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(b.dev(), static_cast<const double2*>(canon), out);
         else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(b.dev(), static_cast<const float2*>(canon), out);
@@ -154,6 +157,7 @@ void half_to_int(const Batch& b, const void* canon, int canon_f64, char* out, cu
 void int_to_half(const Batch& b, const char* in, void* canon, int canon_f64, cudaStream_t st) {
     const int B = 256;
     dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
+    ProfScope prof(PROF_LAYOUT, b.sites() * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
         if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<double2*>(canon));
         else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<float2*>(canon));

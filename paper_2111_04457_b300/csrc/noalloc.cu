@@ -7,6 +7,7 @@
 // file-scope device array of fixed size instead of being allocated.
 #include <cstdio>
 #include <mutex>
+#include <string>
 
 #include "gauge.h"
 #include "kernels.h"
@@ -23,33 +24,67 @@ int set_error(int code, const char* msg);
 
 using namespace bpp;
 
-// 32 MiB per device, held by every GPU that loads the library until exit.
+// 32 MiB per device.  The library is built without relocatable device code,
+// so this file's device code is a module of its own; the array is placed on a
+// device when that module is loaded there (at the first gauge handle created
+// on the device, see noalloc_prepare) and stays until the process exits.
 #define BPP_NOALLOC_SCRATCH_BYTES (32u << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[BPP_NOALLOC_SCRATCH_BYTES];
 
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {};
 
-// Device address of the scratch array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (the first call on that device, which should therefore come
-// before any stream capture) and cached.
-static int noalloc_scratch(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= 64) return set_error(BPP_ERR_UNSUPPORTED, "bpp_dslash_noalloc: device ordinal >= 64");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            char msg[256];
-            std::snprintf(msg, sizeof(msg), "bpp_dslash_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return set_error(BPP_ERR_CUDA, msg);
-        }
-        g_noalloc_ptr[dev] = p;
+// Writes the call's system table: n copies of d, the copy for right-hand side
+// r at byte offset r * field of the scratch vectors.  The descriptor travels
+// as a kernel parameter, so no host buffer has to outlive the call.
+__global__ void k_noalloc_table(SysDesc d, int n, int64_t field, SysDesc* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    SysDesc e = d;
+    e.vec_off = (int64_t)r * field;
+    out[r] = e;
+}
+
+namespace bpp {
+// Device address of the scratch array on device `dev` (which must be the
+// current device).  In host code the array's name is only a host-side
+// stand-in, so the address is looked up with cudaGetSymbolAddress and cached
+// per device.  The lookup also loads the module that holds the array: the
+// library is built without relocatable device code, so this file's device
+// code is a module of its own and, under lazy module loading, its 32 MiB
+// array is only placed on the device at this point.  bpp_gauge_create calls
+// this for its device (it allocates anyway), so a later bpp_dslash_noalloc
+// call, which needs a gauge handle of the same device, finds the array in
+// place and causes no device allocation.
+int noalloc_prepare(int dev, cudaStream_t st, std::string* err, void** ptr) {
+    if (dev < 0 || dev >= 64) {
+        if (err) *err = "device ordinal >= 64";
+        return BPP_ERR_UNSUPPORTED;
     }
-    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev]) {
+        if (ptr) *ptr = g_noalloc_ptr[dev];
+        return BPP_OK;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        if (err) *err = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
+        return BPP_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+    // one launch that writes nothing loads the table kernel as well
+    k_noalloc_table<<<1, 32, 0, st>>>(SysDesc{}, 0, 0, nullptr);
+    count_launch();
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        if (err) *err = std::string("launch of the table kernel failed: ") + cudaGetErrorString(le);
+        return BPP_ERR_CUDA;
+    }
+    if (ptr) *ptr = p;
     return BPP_OK;
 }
+}  // namespace bpp
 
 extern "C" int bpp_dslash_noalloc(bpp_gauge U, const void* psi, void* out, double kappa, int parity, int prec,
                                   int nrhs, bpp_stream stream) {
@@ -75,28 +110,25 @@ extern "C" int bpp_dslash_noalloc(bpp_gauge U, const void* psi, void* out, doubl
                       need, (unsigned)BPP_NOALLOC_SCRATCH_BYTES);
         return set_error(BPP_ERR_INVALID_ARG, msg);
     }
-    unsigned char* base = nullptr;
-    const int rc = noalloc_scratch(dev, &base);
-    if (rc != BPP_OK) return rc;
-
-    SysDesc h[MAXSYS];
-    for (int r = 0; r < nrhs; ++r) {
-        SysDesc& d = h[r];
-        d.g = U->g;
-        for (int p = 0; p < 2; ++p) {
-            for (int mu = 0; mu < 4; ++mu) d.U[p][mu] = link_view(*U, prec, p, mu);
-            d.A[p] = CloverView{nullptr, U->stride};
-            d.Ainv[p] = CloverView{nullptr, U->stride};
-        }
-        d.kappa = kappa;
-        d.vec_off = (int64_t)(r * field);
-        d.stride = U->stride;
-    }
+    std::string err;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // a copy from pageable host memory returns once the table is staged, so the
-    // stack array may go out of scope after the call
-    if (cudaMemcpyAsync(base, h, nrhs * sizeof(SysDesc), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return set_error(BPP_ERR_CUDA, "bpp_dslash_noalloc: upload of the system table failed");
+    void* scratch = nullptr;
+    const int rc = noalloc_prepare(dev, st, &err, &scratch);
+    if (rc != BPP_OK) return set_error(rc, ("bpp_dslash_noalloc: " + err).c_str());
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+
+    SysDesc d;
+    d.g = U->g;
+    for (int p = 0; p < 2; ++p) {
+        for (int mu = 0; mu < 4; ++mu) d.U[p][mu] = link_view(*U, prec, p, mu);
+        d.A[p] = CloverView{nullptr, U->stride};
+        d.Ainv[p] = CloverView{nullptr, U->stride};
+    }
+    d.kappa = kappa;
+    d.vec_off = 0;
+    d.stride = U->stride;
+    k_noalloc_table<<<1, MAXSYS, 0, st>>>(d, nrhs, (int64_t)field, reinterpret_cast<SysDesc*>(base));
+    count_launch();
     const SysDesc* dsys = reinterpret_cast<const SysDesc*>(base);
     char* vin = reinterpret_cast<char*>(base + table);
     char* vout = vin + (size_t)nrhs * field;

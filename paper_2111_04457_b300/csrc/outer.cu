@@ -144,6 +144,7 @@ __global__ void k_oc_loop(OuterCtl* oc, unsigned long long h_outer) {
 
 #define OC_LAUNCH(...)                           \
     do {                                         \
+        ProfScope prof_(PROF_CTL, 0.0, st);      \
         __VA_ARGS__;                             \
         count_launch();                          \
         BPP_CHECK_LAUNCH();                      \

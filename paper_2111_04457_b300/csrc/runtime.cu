@@ -108,9 +108,9 @@ struct ProfRec {
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfRec> g_prof;
-static int64_t g_prof_n[NPREC] = {};
-static double g_prof_ms[NPREC] = {};
-static double g_prof_bytes[NPREC] = {};
+static int64_t g_prof_n[NPROF] = {};
+static double g_prof_ms[NPROF] = {};
+static double g_prof_bytes[NPROF] = {};
 
 ProfScope::ProfScope(int p, double b, cudaStream_t st) : prec(p), bytes(b), s(st), on(false) {
     {
@@ -154,7 +154,7 @@ int prof_enable(int on) {
 int prof_read(int prec, int64_t* n, double* ms, double* bytes, int reset) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof_drain_locked();
-    if (prec < 0 || prec >= NPREC) return BPP_ERR_INVALID_ARG;
+    if (prec < 0 || prec >= NPROF) return BPP_ERR_INVALID_ARG;
     if (n) *n = g_prof_n[prec];
     if (ms) *ms = g_prof_ms[prec];
     if (bytes) *bytes = g_prof_bytes[prec];

@@ -21,6 +21,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
 void drop_plans(const Gauge* G);
 
 // Link gradient / projected force (see bpp_force).
-void force(const Gauge& G, const void* x, const void* lam, double kappa, void* dU, int project, cudaStream_t st);
+void force(const Gauge& G, const void* x, const void* lam, double kappa, double csw, int nrhs, void* dU, int project,
+           cudaStream_t st);
 
 }  // namespace bpp

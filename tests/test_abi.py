@@ -56,3 +56,18 @@ def test_gauge_create_rejects_bad_lattices_before_touching_the_gpu():
         assert rc == -1, (L, bc)
     rc = lib.bpp_gauge_create(None, dummy, None, ctypes.byref(h))
     assert rc == -1
+
+
+def test_prof_classes_without_gpu():
+    """Every documented kernel class (0..9) reads back as zero launches before
+    any launch; a class out of range is refused with INVALID_ARG."""
+    import pytest
+
+    import paper_2111_04457_b300 as bpp
+    for c in range(10):
+        n, ms, by = bpp.prof_read(c, reset=True)
+        assert n == 0 and ms == 0.0 and by == 0.0
+    for c in (-1, 10):
+        with pytest.raises(bpp.BppError) as e:
+            bpp.prof_read(c)
+        assert e.value.code == -1

@@ -95,3 +95,55 @@ def test_clover_grad_b():
     for r in range(2):
         lam_ref = oracle.solve(U0, eta[r], KAPPA, L, BC, F=F, tol=1e-12, dagger=True)
         assert rel_err(to_np(b.grad[r]), lam_ref) <= 1e-8
+
+
+def test_autograd_clover_fd_4x4():
+    """Wilson-clover (c_SW = 1): grad_U through torch.autograd (hopping and
+    clover parts of the force) against central finite differences of the loss
+    in one random complex direction of all links, and in su(3) directions of
+    16 random links; grad_b in one random direction."""
+    bpp = lib()
+    L = (4, 4, 4, 4)
+    csw = 1.0
+    U0 = synth.random_links(L)
+    b0 = synth.gaussian_spinor(L, seed=2)
+    eta = to_dev(synth.gaussian_spinor(L, seed=3))
+
+    def loss_c(U, b):
+        from paper_2111_04457_b300.autograd import solve_fn
+        x = solve_fn(U, b, L, KAPPA, csw=csw, tol=1e-13, inner_prec=0)
+        return torch.vdot(eta.reshape(-1), x.reshape(-1)).real
+
+    U = to_dev(U0).requires_grad_(True)
+    b = to_dev(b0).requires_grad_(True)
+    loss_c(U, b).backward()
+    gU, gb = U.grad.clone(), b.grad.clone()
+    rng = np.random.default_rng(11)
+    h = 1e-4
+    with torch.no_grad():
+        d = to_dev(rng.normal(size=b0.shape) + 1j * rng.normal(size=b0.shape))
+        fd = (loss_c(U, b + h * d) - loss_c(U, b - h * d)) / (2 * h)
+        an = torch.vdot(gb.reshape(-1), d.reshape(-1)).real
+        assert abs(float(fd - an)) <= 1e-6 * abs(float(an))
+        E = to_dev(rng.normal(size=U0.shape) + 1j * rng.normal(size=U0.shape))
+        fd = (loss_c(U + h * E, b) - loss_c(U - h * E, b)) / (2 * h)
+        an = torch.vdot(gU.reshape(-1), E.reshape(-1)).real
+        assert abs(float(fd - an)) <= 1e-6 * abs(float(an))
+        g = bpp.Gauge(U.detach(), L)
+        g.clover_build(KAPPA, csw)
+        x, _ = bpp.solve(g, b.detach(), KAPPA, csw, 1e-12, bpp.solve_opts(inner_prec=0))
+        lam, _ = bpp.solve(g, eta, KAPPA, csw, 1e-12, bpp.solve_opts(inner_prec=0, dagger=True))
+        P = to_np(bpp.force(g, x, lam, KAPPA, project=True, csw=csw))
+        V = oracle.volume(L)
+        from scipy.linalg import expm
+        for _ in range(16):
+            mu, s = rng.integers(0, 4), rng.integers(0, V)
+            A = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+            T = 0.5 * (A + A.conj().T)
+            T -= np.trace(T) / 3 * np.eye(3)
+            Up, Um = U0.copy(), U0.copy()
+            Up[mu, s] = expm(1j * h * T) @ U0[mu, s]
+            Um[mu, s] = expm(-1j * h * T) @ U0[mu, s]
+            fd = (loss_c(to_dev(Up), b) - loss_c(to_dev(Um), b)) / (2 * h)
+            an = np.trace(T @ P[mu, s]).real
+            assert abs(float(fd) - an) <= 1e-6 * max(abs(an), 1e-2)
