@@ -232,6 +232,30 @@ void bpp_solve_opts_default(bpp_solve_opts* opts);
 int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs,
               const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream);
 
+/* Operator modes of the lexical solve (Fig. 1: "mode is D, Ddag, DdagD"). */
+typedef enum { BPP_LEX_D = 0, BPP_LEX_DDAG = 1, BPP_LEX_DDAGD = 2 } bpp_lex_mode;
+
+/* Lexical propagator solve (Fig. 1, Fprop_Standard_lex with the double/float
+ * mixed-precision solver of Sec. 2): A x = b on the full lattice, without
+ * even-odd preconditioning, for nrhs right-hand sides sharing the gauge field:
+ *   mode BPP_LEX_D:     A = D      (opts->solver BPP_BICGSTAB: BiCGStab on D;
+ *                                   BPP_CGNR: CG on D^dag D x = D^dag b, the
+ *                                   normal-equation propagator x = D^{-1} b)
+ *   mode BPP_LEX_DDAG:  A = D^dag  (likewise)
+ *   mode BPP_LEX_DDAGD: A = D^dag D (CG; opts->solver is ignored)
+ * D is Eq. (1) with the clover term when csw != 0 (requires bpp_clover_build
+ * with the same kappa and csw).  Outer loop: FP64 defect correction
+ * r = b - A x with the full FP64 operator, inner solve of A e = r/|r| in
+ * opts->inner_prec (BPP_F32, or BPP_F64 for the plain solve; BPP_F16 and
+ * BPP_F64DF return BPP_ERR_UNSUPPORTED), x += |r| e, until
+ * |b - A x| / |b| <= tol (FP64, recomputed from scratch), reported per RHS
+ * as stats[r].true_resid.  opts->use_graph and opts->outer_arith are ignored
+ * (host-driven loop, convergence read every check_every inner iterations).
+ * b, x: complex128 [nrhs][V][4][3], device or host memory.  Synchronises
+ * `stream`.  Errors: as bpp_solve. */
+int bpp_solve_lex(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs, int mode,
+                  const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream);
+
 /* Batched solve over nlat independent lattices (each with its own gauge
  * handle, hopping parameter kappa[i] and one right-hand side), run together so
  * every kernel launch covers all lattices.  csw != 0: Wilson-clover, each

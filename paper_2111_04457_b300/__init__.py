@@ -29,6 +29,7 @@ if not os.path.exists(_SO):
 _lib = ctypes.CDLL(_SO)
 
 F64, F32, F16, F64DF = 0, 1, 2, 3
+LEX_D, LEX_DDAG, LEX_DDAGD = 0, 1, 2
 EVEN, ODD, FULL = 0, 1, 2
 BICGSTAB, CGNR = 0, 1
 _ERR = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
@@ -79,6 +80,7 @@ _SIGS = {
     "bpp_dirac_apply": ([_p, _p, _p, _d, _d, _i, _i, _p], _i),
     "bpp_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
     "bpp_solve": ([_p, _p, _p, _d, _d, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
+    "bpp_solve_lex": ([_p, _p, _p, _d, _d, _d, _i, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_solve_batch": ([_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_d), _d, _d,
                          ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_force": ([_p, _p, _p, _d, _d, _i, _p, _i, _p], _i),
@@ -335,6 +337,30 @@ def solve(g: Gauge, b: torch.Tensor, kappa: float, csw: float = 0.0, tol: float 
     st = (SolveStats * n)()
     rc = _lib.bpp_solve(g.handle, _ptr(b), _ptr(x), float(kappa), float(csw), float(tol), n, ctypes.byref(o), st,
                         _stream(stream))
+    stats = [s.as_dict() for s in st]
+    if raise_on_fail:
+        _check(rc)
+    return x, stats
+
+
+def solve_lex(g: Gauge, b: torch.Tensor, kappa: float, csw: float = 0.0, tol: float = 1e-10, mode: int = LEX_D,
+              opts: SolveOpts = None, x: torch.Tensor = None, stream=None, raise_on_fail: bool = True):
+    """Full-lattice (lexical) solve of A x = b with A = D (mode LEX_D), D^dag
+    (LEX_DDAG) or D^dag D (LEX_DDAGD, CG); with opts.solver = CGNR and mode
+    LEX_D, x = D^-1 b through CG on the normal equations.  FP64 defect
+    correction around an FP32 (or FP64) inner solve to |b - A x| / |b| <= tol.
+    b: complex128 [nrhs][V][4][3] (or [V][4][3]), device or host.
+    Returns (x, [stats dict per RHS])."""
+    if b.dtype != torch.complex128:
+        raise ValueError("b must be complex128")
+    b = b.contiguous()
+    n = _nrhs(b, 12 * g.lattice.V)
+    if x is None:
+        x = torch.empty_like(b)
+    o = opts if opts is not None else solve_opts()
+    st = (SolveStats * n)()
+    rc = _lib.bpp_solve_lex(g.handle, _ptr(b), _ptr(x), float(kappa), float(csw), float(tol), n, int(mode),
+                            ctypes.byref(o), st, _stream(stream))
     stats = [s.as_dict() for s in st]
     if raise_on_fail:
         _check(rc)

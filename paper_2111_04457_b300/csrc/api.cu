@@ -311,6 +311,49 @@ int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, dou
     });
 }
 
+int bpp_solve_lex(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs, int mode,
+                  const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream) {
+    return guard("bpp_solve_lex", [&]() -> int {
+        check_gauge(U);
+        check_clover(*U, kappa, csw);
+        BPP_REQUIRE(b && x, BPP_ERR_INVALID_ARG, "NULL field");
+        BPP_REQUIRE(nrhs >= 1 && nrhs <= MAXSYS, BPP_ERR_INVALID_ARG, "nrhs must be 1..64");
+        BPP_REQUIRE(std::isfinite(kappa), BPP_ERR_INVALID_ARG, "kappa must be finite");
+        bpp_solve_opts o;
+        bpp_solve_opts_default(&o);
+        if (opts) o = *opts;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        const size_t field = (size_t)U->V * 12 * 16;
+        const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+        DevBuf bbuf, xbuf;
+        const char* bp = static_cast<const char*>(b);
+        char* xp = static_cast<char*>(x);
+        if (!bdev) {
+            bbuf.alloc(field * nrhs, st);
+            BPP_CUDA(cudaMemcpyAsync(bbuf.p, b, field * nrhs, cudaMemcpyHostToDevice, st));
+            bp = bbuf.as<char>();
+        }
+        if (!xdev) {
+            xbuf.alloc(field * nrhs, st);
+            if (o.use_x0) BPP_CUDA(cudaMemcpyAsync(xbuf.p, x, field * nrhs, cudaMemcpyHostToDevice, st));
+            xp = xbuf.as<char>();
+        }
+        std::vector<const void*> bv(nrhs);
+        std::vector<void*> xv(nrhs);
+        for (int r = 0; r < nrhs; ++r) {
+            bv[r] = bp + field * r;
+            xv[r] = xp + field * r;
+        }
+        int rc = solve_lex(*U, kappa, csw != 0.0, bv, xv, mode, tol, o, stats, st);
+        if (!xdev) {
+            BPP_CUDA(cudaMemcpyAsync(x, xp, field * nrhs, cudaMemcpyDeviceToHost, st));
+            BPP_CUDA(cudaStreamSynchronize(st));
+        }
+        if (rc != BPP_OK) return fail(rc, "bpp_solve_lex: a right-hand side did not reach the tolerance (see stats)");
+        return BPP_OK;
+    });
+}
+
 int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* const* x, const double* kappa,
                     double csw, double tol, const bpp_solve_opts* opts, bpp_solve_stats* stats, bpp_stream stream) {
     return guard("bpp_solve_batch", [&]() -> int {

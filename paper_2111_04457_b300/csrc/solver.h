@@ -17,6 +17,12 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                 const std::vector<const void*>& b_canon, const std::vector<void*>& x_canon, double tol,
                 const bpp_solve_opts& o, bpp_solve_stats* stats, cudaStream_t st);
 
+// Full-lattice (lexical) solve of A x = b, A = D, D^dag or D^dag D (mode
+// bpp_lex_mode), FP64 defect correction around an FP64 or FP32 inner solve.
+int solve_lex(const Gauge& G, double kappa, bool clover, const std::vector<const void*>& b_canon,
+              const std::vector<void*>& x_canon, int mode, double tol, const bpp_solve_opts& o,
+              bpp_solve_stats* stats, cudaStream_t st);
+
 // Releases cached solver plans that use gauge G (all plans for G == nullptr).
 void drop_plans(const Gauge* G);
 
