@@ -290,6 +290,58 @@ int bpp_solve_batch(int nlat, const bpp_gauge* U, const void* const* b, void* co
 int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, double csw, int nrhs, void* dU,
               int project_su3, bpp_stream stream);
 
+/* ---- Domain decomposition (Sec. 2 and Sec. 3.1: sub-lattices per process,
+ * boundary exchange, global sums), here with every sub-lattice on the current
+ * GPU.  The lattice is cut in x4 into ndom slabs of L[3] / ndom time slices
+ * (an even number, so each slab keeps the global even-odd split); each slab
+ * holds only its own links.  A decomposed hop packs each slab's two faces of
+ * the input field (the bottom face's (1 + SF gamma_4) projections and the top
+ * face's U_4^dag (1 - SF gamma_4) projections, 12 reals per face site;
+ * SF = -1 for D, +1 for D^dag), copies them into the neighbouring slabs' own
+ * buffers (device-to-device copies standing in for the messages), and runs
+ * the hopping kernel on every slab with the face terms from those buffers.
+ * The face values carry exactly the arithmetic of the undecomposed kernel, so
+ * the decomposed hopping term and Schur operator equal bpp_dslash and
+ * bpp_schur_apply bit for bit.  Wilson fermions (no clover term). */
+typedef struct bpp_dd_s* bpp_dd;
+
+/* Combines per-slab sums: in holds nparts blocks of n doubles (slab order),
+ * out receives their element-wise sum (n doubles); returns 0 on success.  The
+ * hook where a multi-process run adds its cross-process sum. */
+typedef int (*bpp_dd_reducer)(const double* in, double* out, int nparts, int n, void* ctx);
+
+/* Cuts the lattice lat (links U_lex as in bpp_gauge_create, device or host)
+ * into ndom slabs in x4.  Errors: INVALID_ARG (ndom outside 2..64, L[3] / ndom
+ * not an even whole number, or the bpp_gauge_create conditions), OOM, CUDA. */
+int bpp_dd_create(const bpp_lattice* lat, const void* U_lex, int ndom, bpp_stream stream, bpp_dd* out);
+int bpp_dd_destroy(bpp_dd dd);
+
+/* Registers the reducer of the decomposed solve's sums (NULL: the library sums
+ * the slabs on the device, in slab order).  The library calls it from the
+ * calling thread with host buffers, after synchronising the stream. */
+int bpp_dd_set_reducer(bpp_dd dd, bpp_dd_reducer fn, void* ctx);
+
+/* The hopping term of bpp_dslash (parity BPP_EVEN or BPP_ODD, prec BPP_F64,
+ * BPP_F32 or BPP_F16, canonical global half fields [nrhs][Vh][4][3] in device
+ * memory) through the decomposition.  Errors: INVALID_ARG, OOM, CUDA. */
+int bpp_dd_dslash(bpp_dd dd, const void* psi, void* out, double kappa, int parity, int prec, int nrhs,
+                  bpp_stream stream);
+
+/* The Wilson Schur operator Mhat = 1 - kappa^2 H_eo H_oe (or Mhat^dag) of
+ * bpp_schur_apply through the decomposition (two decomposed hops). */
+int bpp_dd_schur_apply(bpp_dd dd, const void* in, void* out, double kappa, int dagger, int prec, int nrhs,
+                       bpp_stream stream);
+
+/* Solves D x = b (opts->dagger: D^dag x = b) for the Wilson matrix through the
+ * decomposition: FP64 BiCGStab on the even-odd Schur system
+ * (opts->inner_prec must be BPP_F64, opts->solver BPP_BICGSTAB), every inner
+ * product reduced per slab and combined across slabs (see the reducer), then
+ * x_o reconstructed and the full FP64 residual ||b - D x|| / ||b|| computed
+ * the same way (stats[r].true_resid).  b, x: device complex128
+ * [nrhs][V][4][3].  Synchronises `stream`.  Errors: as bpp_solve. */
+int bpp_dd_solve(bpp_dd dd, const void* b, void* x, double kappa, double tol, int nrhs, const bpp_solve_opts* opts,
+                 bpp_solve_stats* stats, bpp_stream stream);
+
 /* Number of kernels this library has launched since load (or since the last
  * reset when reset != 0); graph launches count each kernel node they run. */
 int64_t bpp_launch_count(int reset);

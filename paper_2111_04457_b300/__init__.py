@@ -84,6 +84,12 @@ _SIGS = {
     "bpp_solve_batch": ([_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_d), _d, _d,
                          ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_force": ([_p, _p, _p, _d, _d, _i, _p, _i, _p], _i),
+    "bpp_dd_create": ([ctypes.POINTER(_Lattice), _p, _i, _p, ctypes.POINTER(_p)], _i),
+    "bpp_dd_destroy": ([_p], _i),
+    "bpp_dd_set_reducer": ([_p, _p, _p], _i),
+    "bpp_dd_dslash": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
+    "bpp_dd_schur_apply": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
+    "bpp_dd_solve": ([_p, _p, _p, _d, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_launch_count": ([_i], _i64),
     "bpp_prof_enable": ([_i], _i),
     "bpp_prof_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), ctypes.POINTER(_d), _i], _i),
@@ -406,6 +412,108 @@ def force(g: Gauge, x: torch.Tensor, lam: torch.Tensor, kappa: float, project: b
     _check(_lib.bpp_force(g.handle, _ptr(x), _ptr(lam), float(kappa), float(csw), n, _ptr(out), int(project),
                           _stream(stream)))
     return out
+
+
+# Reducer of the decomposed solve's sums: (in, out, nparts, n, ctx) -> int
+DD_REDUCER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_int, ctypes.c_int, ctypes.c_void_p)
+
+
+class DomainDecomposition:
+    """The lattice cut in x4 into ndom slabs (L4 / ndom even), each slab
+    holding its own links, all on the current GPU (bpp_dd_*).  The decomposed
+    hopping term and Schur operator equal dslash() and schur_apply() bit for
+    bit; solve() is FP64 BiCGStab on the Schur system with per-slab
+    reductions combined across slabs.
+
+    U: complex128 [4][V][3][3] (CUDA or CPU)."""
+
+    def __init__(self, U: torch.Tensor, L, ndom: int, bc=(1, 1, 1, -1), stream=None):
+        self.lattice = Lattice(tuple(int(v) for v in L), tuple(int(v) for v in bc))
+        if U.dtype != torch.complex128 or tuple(U.shape) != (4, self.lattice.V, 3, 3):
+            raise ValueError("U must be complex128 of shape (4, V, 3, 3)")
+        U = U.contiguous()
+        lat = _Lattice((ctypes.c_int * 4)(*self.lattice.L), (ctypes.c_int * 4)(*self.lattice.bc))
+        h = _p()
+        _check(_lib.bpp_dd_create(ctypes.byref(lat), _ptr(U), int(ndom), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.ndom = int(ndom)
+        self._reducer = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("decomposition handle destroyed")
+        return self._h
+
+    def set_reducer(self, fn=None):
+        """fn(parts: numpy [nparts, n] float64) -> numpy [n] float64 combines the
+        per-slab sums (None: the library's device sum in slab order)."""
+        if fn is None:
+            self._reducer = None
+            _check(_lib.bpp_dd_set_reducer(self.handle, None, None))
+            return
+        import numpy as np
+
+        def cb(pin, pout, nparts, n, ctx):
+            try:
+                parts = np.ctypeslib.as_array(pin, shape=(nparts * n,)).reshape(nparts, n).copy()
+                res = np.asarray(fn(parts), dtype=np.float64).reshape(n)
+                np.ctypeslib.as_array(pout, shape=(n,))[:] = res
+                return 0
+            except Exception:
+                return 1
+        self._reducer = DD_REDUCER(cb)     # kept alive with the handle
+        _check(_lib.bpp_dd_set_reducer(self.handle, ctypes.cast(self._reducer, _p), None))
+
+    def dslash(self, psi: torch.Tensor, kappa: float, parity: int, prec: int = F64, stream=None):
+        _cuda(psi, "psi")
+        if psi.dtype != _cdtype(prec):
+            raise ValueError(f"psi must be {_cdtype(prec)} for precision {prec}")
+        psi = psi.contiguous()
+        n = _nrhs(psi, 12 * self.lattice.Vh)
+        out = torch.empty_like(psi)
+        _check(_lib.bpp_dd_dslash(self.handle, _ptr(psi), _ptr(out), float(kappa), parity, prec, n, _stream(stream)))
+        return out
+
+    def schur_apply(self, x: torch.Tensor, kappa: float, dagger: bool = False, prec: int = F64, stream=None):
+        _cuda(x, "x")
+        if x.dtype != _cdtype(prec):
+            raise ValueError(f"x must be {_cdtype(prec)}")
+        x = x.contiguous()
+        n = _nrhs(x, 12 * self.lattice.Vh)
+        out = torch.empty_like(x)
+        _check(_lib.bpp_dd_schur_apply(self.handle, _ptr(x), _ptr(out), float(kappa), int(dagger), prec, n,
+                                       _stream(stream)))
+        return out
+
+    def solve(self, b: torch.Tensor, kappa: float, tol: float = 1e-10, opts: SolveOpts = None, stream=None,
+              raise_on_fail: bool = True):
+        _cuda(b, "b")
+        if b.dtype != torch.complex128:
+            raise ValueError("b must be complex128")
+        b = b.contiguous()
+        n = _nrhs(b, 12 * self.lattice.V)
+        x = torch.empty_like(b)
+        o = opts if opts is not None else solve_opts(inner_prec=F64)
+        st = (SolveStats * n)()
+        rc = _lib.bpp_dd_solve(self.handle, _ptr(b), _ptr(x), float(kappa), float(tol), n, ctypes.byref(o), st,
+                               _stream(stream))
+        stats = [s.as_dict() for s in st]
+        if raise_on_fail:
+            _check(rc)
+        return x, stats
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.bpp_dd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def exported_symbols():

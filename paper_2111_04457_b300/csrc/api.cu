@@ -9,6 +9,7 @@
 #include "gauge.h"
 #include "kernels.h"
 #include "solver.h"
+#include "dd.h"
 
 namespace bpp {
 int prof_enable(int on);
@@ -391,6 +392,60 @@ int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, double 
         BPP_REQUIRE(is_device_ptr(x) && is_device_ptr(lam) && is_device_ptr(dU), BPP_ERR_INVALID_ARG,
                     "x, lam and dU must be device memory");
         force(*U, x, lam, kappa, csw, nrhs, dU, project_su3 ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
+        return BPP_OK;
+    });
+}
+
+int bpp_dd_create(const bpp_lattice* lat, const void* U_lex, int ndom, bpp_stream stream, bpp_dd* out) {
+    return guard("bpp_dd_create", [&]() -> int {
+        dd_create(lat, U_lex, ndom, reinterpret_cast<cudaStream_t>(stream), out);
+        return BPP_OK;
+    });
+}
+
+int bpp_dd_destroy(bpp_dd dd) {
+    return guard("bpp_dd_destroy", [&]() -> int {
+        dd_destroy(dd);
+        return BPP_OK;
+    });
+}
+
+int bpp_dd_set_reducer(bpp_dd dd, bpp_dd_reducer fn, void* ctx) {
+    return guard("bpp_dd_set_reducer", [&]() -> int {
+        dd_set_reducer(dd, fn, ctx);
+        return BPP_OK;
+    });
+}
+
+int bpp_dd_dslash(bpp_dd dd, const void* psi, void* out, double kappa, int parity, int prec, int nrhs,
+                  bpp_stream stream) {
+    return guard("bpp_dd_dslash", [&]() -> int {
+        BPP_REQUIRE(psi && out && psi != out, BPP_ERR_INVALID_ARG, "NULL or aliased field");
+        dd_dslash(dd, psi, out, kappa, parity, prec, nrhs, reinterpret_cast<cudaStream_t>(stream));
+        return BPP_OK;
+    });
+}
+
+int bpp_dd_schur_apply(bpp_dd dd, const void* in, void* out, double kappa, int dagger, int prec, int nrhs,
+                       bpp_stream stream) {
+    return guard("bpp_dd_schur_apply", [&]() -> int {
+        BPP_REQUIRE(in && out && in != out, BPP_ERR_INVALID_ARG, "NULL or aliased field");
+        dd_schur(dd, in, out, kappa, dagger ? 1 : 0, prec, nrhs, reinterpret_cast<cudaStream_t>(stream));
+        return BPP_OK;
+    });
+}
+
+int bpp_dd_solve(bpp_dd dd, const void* b, void* x, double kappa, double tol, int nrhs, const bpp_solve_opts* opts,
+                 bpp_solve_stats* stats, bpp_stream stream) {
+    return guard("bpp_dd_solve", [&]() -> int {
+        BPP_REQUIRE(b && x && is_device_ptr(b) && is_device_ptr(x), BPP_ERR_INVALID_ARG, "b and x must be device memory");
+        BPP_REQUIRE(std::isfinite(kappa), BPP_ERR_INVALID_ARG, "kappa must be finite");
+        bpp_solve_opts o;
+        bpp_solve_opts_default(&o);
+        o.inner_prec = BPP_F64;
+        if (opts) o = *opts;
+        const int rc = dd_solve(dd, b, x, kappa, tol, nrhs, o, stats, reinterpret_cast<cudaStream_t>(stream));
+        if (rc != BPP_OK) return fail(rc, "bpp_dd_solve: a right-hand side did not reach the tolerance (see stats)");
         return BPP_OK;
     });
 }

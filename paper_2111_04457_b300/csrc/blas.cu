@@ -35,6 +35,7 @@ struct BlasParams {
     KScal* sc;
     double* partials;
     unsigned* tickets;
+    double* red_out = nullptr;   // set: write the system's sums here [s][4], do not finalize
 };
 
 __device__ __forceinline__ void check_done(KScal& k) {
@@ -147,34 +148,10 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
     }
 }
 
-// Each block covers BLAS_SPT * BLAS_B sites of one system, so the last block
-// of a reduction sums few per-block partials.
-template <int P, int OP>
-__global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
-    int s, tile;
-    map_block(bp.map, s, tile);
-    const SysDesc& d = bp.sys[s];
-    KScal* K = bp.sc + s;
-    const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2 || OP == B_NORM2X2) || !K->done;
-    // scalars used by the update (read before any finalize of this launch)
-    const double2 al = K->alpha, om = K->omega, be = K->beta;
-    using real = typename PT<P>::real;
-    real red[4] = {0, 0, 0, 0};
-    if (active) {
-        const int base = tile * (BLAS_SPT * BLAS_B) + threadIdx.x;
-#pragma unroll
-        for (int k = 0; k < BLAS_SPT; ++k) {
-            const int i = base + k * BLAS_B;
-            if (i < d.g.Vh) blas_site<P, OP>(bp, d, i, al, om, be, red);
-        }
-    }
-    constexpr bool HAS_RED = OP != B_S && OP != B_P;
-    if (!HAS_RED) return;
-    if (!active) return;   // whole system inactive: every block of it returns here
-    double tot[4];
-    if (!reduce_sys<4, real>(RedCtx{bp.map, bp.partials, bp.tickets}, s, red, tot)) return;
-    if (threadIdx.x != 0) return;
-    KScal& k = *K;
+// Solver scalars from the reduced sums tot[] of one system (the end of a
+// fused vector kernel, or of a decomposed reduction).
+template <int OP>
+__device__ void blas_finalize(KScal& k, const double tot[4]) {
     if (OP == B_INIT_BICG) {
         k.bb = tot[0];
         k.rr = tot[0];
@@ -225,6 +202,51 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     }
 }
 
+// Finalize of a reduction whose sums were combined elsewhere (one thread per
+// system).
+template <int OP>
+__global__ void k_blas_fin(KScal* sc, const double* tot, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    if (!(OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2 || OP == B_NORM2X2) && sc[s].done) return;
+    blas_finalize<OP>(sc[s], tot + 4 * s);
+}
+
+// Each block covers BLAS_SPT * BLAS_B sites of one system, so the last block
+// of a reduction sums few per-block partials.
+template <int P, int OP>
+__global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
+    int s, tile;
+    map_block(bp.map, s, tile);
+    const SysDesc& d = bp.sys[s];
+    KScal* K = bp.sc + s;
+    const bool active = (OP == B_INIT_BICG || OP == B_CG_INIT || OP == B_NORM2 || OP == B_NORM2X2) || !K->done;
+    // scalars used by the update (read before any finalize of this launch)
+    const double2 al = K->alpha, om = K->omega, be = K->beta;
+    using real = typename PT<P>::real;
+    real red[4] = {0, 0, 0, 0};
+    if (active) {
+        const int base = tile * (BLAS_SPT * BLAS_B) + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < BLAS_SPT; ++k) {
+            const int i = base + k * BLAS_B;
+            if (i < d.g.Vh) blas_site<P, OP>(bp, d, i, al, om, be, red);
+        }
+    }
+    constexpr bool HAS_RED = OP != B_S && OP != B_P;
+    if (!HAS_RED) return;
+    if (!active) return;   // whole system inactive: every block of it returns here
+    double tot[4];
+    if (!reduce_sys<4, real>(RedCtx{bp.map, bp.partials, bp.tickets}, s, red, tot)) return;
+    if (threadIdx.x != 0) return;
+    if (bp.red_out) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bp.red_out[4 * s + k] = tot[k];
+        return;
+    }
+    blas_finalize<OP>(*K, tot);
+}
+
 // p = z + beta p for CGNR (separate: needs the finalised beta)
 template <int P>
 __global__ void __launch_bounds__(BLAS_B) k_cg_p(BlasParams bp) {
@@ -248,8 +270,11 @@ __global__ void __launch_bounds__(BLAS_B) k_cg_p(BlasParams bp) {
 }
 
 template <int P>
-static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st) {
+static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st,
+                   double* red_out) {
+    BPP_REQUIRE(!red_out || op != B_CG_BETA, BPP_ERR_UNSUPPORTED, "CG beta update has no deferred form");
     BlasParams bp;
+    bp.red_out = red_out;
     bp.sys = bt.dev();
     int nb = 0;
     bp.map = block_map(bt, BLAS_B * BLAS_SPT, nb);
@@ -285,11 +310,26 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
     BPP_CHECK_LAUNCH();
 }
 
-void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st) {
+void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st, double* red_out) {
     BPP_REQUIRE(bt.prec != P64S, BPP_ERR_UNSUPPORTED, "Krylov vector kernels do not run on split-FP64 vectors");
-    if (bt.prec == P64) blas_t<P64>(bt, op, vv, sc, rb, st);
-    else if (bt.prec == P32) blas_t<P32>(bt, op, vv, sc, rb, st);
-    else blas_t<P16>(bt, op, vv, sc, rb, st);
+    if (bt.prec == P64) blas_t<P64>(bt, op, vv, sc, rb, st, red_out);
+    else if (bt.prec == P32) blas_t<P32>(bt, op, vv, sc, rb, st, red_out);
+    else blas_t<P16>(bt, op, vv, sc, rb, st, red_out);
+}
+
+void blas_fin(int op, KScal* sc, const double* tot, int n, cudaStream_t st) {
+    ProfScope prof(PROF_CTL, 0.0, st);
+    switch (op) {
+        case B_INIT_BICG: k_blas_fin<B_INIT_BICG><<<1, 64, 0, st>>>(sc, tot, n); break;
+        case B_ALPHA: k_blas_fin<B_ALPHA><<<1, 64, 0, st>>>(sc, tot, n); break;
+        case B_OMEGA: k_blas_fin<B_OMEGA><<<1, 64, 0, st>>>(sc, tot, n); break;
+        case B_XR: k_blas_fin<B_XR><<<1, 64, 0, st>>>(sc, tot, n); break;
+        case B_NORM2: k_blas_fin<B_NORM2><<<1, 64, 0, st>>>(sc, tot, n); break;
+        case B_NORM2X2: k_blas_fin<B_NORM2X2><<<1, 64, 0, st>>>(sc, tot, n); break;
+        default: throw Error(BPP_ERR_UNSUPPORTED, "no deferred finalize for this vector operation");
+    }
+    count_launch();
+    BPP_CHECK_LAUNCH();
 }
 
 // ----------------------------------------------------------------------------- outer loop
@@ -303,6 +343,7 @@ struct OuterParams {
     KScal* sc;
     double* partials;
     unsigned* tickets;
+    double* red_out = nullptr;   // set (residual kernels): write the sums here [s][4] instead of sc
 };
 
 __global__ void __launch_bounds__(BLAS_B) k_outer_residual(OuterParams op) {
@@ -323,6 +364,10 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_residual(OuterParams op) {
     double tot[4];
     if (!reduce_sys<4, double>(RedCtx{op.map, op.partials, op.tickets}, s, red, tot)) return;
     if (threadIdx.x == 0) {
+        if (op.red_out) {
+            for (int k = 0; k < 4; ++k) op.red_out[4 * s + k] = tot[k];
+            return;
+        }
         op.sc[s].rr = tot[0];
         op.sc[s].scale = sqrt(tot[0]);
     }
@@ -699,8 +744,10 @@ void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal*
     BPP_CHECK_LAUNCH();
 }
 
-void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st) {
+void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st,
+                    double* red_out) {
     OuterParams op;
+    op.red_out = red_out;
     op.s64 = b64.dev();
     op.sP = b64.dev();
     int nb = 0;

@@ -58,12 +58,20 @@ struct BlasVecs {
          *b = nullptr, *w = nullptr, *z = nullptr;
 };
 
-void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st);
+// With red_out set, the reducing operations write each system's sums
+// (4 doubles per system) to red_out instead of deriving the scalars; blas_fin
+// then derives them from combined sums (a reduction across the domains of a
+// decomposition).  Every operation except B_CG_BETA has this form.
+void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st,
+          double* red_out = nullptr);
+void blas_fin(int op, KScal* sc, const double* tot, int n, cudaStream_t st);
 
 // Outer defect-correction steps (FP64 batch b64 and inner-precision batch bP
 // over the same systems):
 // r64 = bhat - r64 (r64 holds Mhat x on entry); sc.rr = ||r64||^2, sc.scale = ||r64||
-void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st);
+// (red_out set: ||r64||^2 is written to red_out[4 s] instead of the scalars)
+void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& rb, cudaStream_t st,
+                    double* red_out = nullptr);
 // lo = r / scale (converted to the inner precision); r is FP64, or split FP64
 // when split is set
 void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st,

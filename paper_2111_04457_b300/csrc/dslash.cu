@@ -339,7 +339,45 @@ template <> struct HopMaxThreads<P16> { static constexpr int value = BPP_HOP16_M
 template <int P> struct HopMinBlocks { static constexpr int value = 1; };
 template <> struct HopMinBlocks<P64S> { static constexpr int value = BPP_HOPDF_MINB; };
 
-template <int P, bool DAG, int MODE>
+// Face terms of a domain decomposition in x4 (see HopParams).  Forward hop at
+// the top face: the upper domain sent h = (1 + SF gamma_4) psi (and, FP16, the
+// site's spinor scale, applied to the link as in decode); backward hop at the
+// bottom face: the lower domain sent g = U^dag (1 - SF gamma_4) psi.  The
+// arithmetic and its order are those of hop_term, so the result is the same
+// to the bit as without the decomposition.
+template <int P, int SF>
+__device__ __forceinline__ void hop_halo_fwd(cx<typename PT<P>::real> acc[12], const HopParams& hp, int s, int64_t f,
+                                             const LinkView& U, int64_t i, bool flip) {
+    using real = typename PT<P>::real;
+    const cx<real>* hb = static_cast<const cx<real>*>(hp.halo_fwd) + (int64_t)s * 6 * hp.face;
+    cx<real> h[6], u[9], g[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = hb[k * hp.face + f];
+    Access<P>::load_link(U, i, u);
+    if (P == P16) {
+        const float sc = hp.halo_fwd_scale[(int64_t)s * hp.face + f];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k] = mkc<real>(u[k].r * sc, u[k].i * sc);
+    }
+    if (flip) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = -h[k];
+    }
+    link_mul<false>(u, h, g);
+    reconstruct<3, SF>(acc, g);
+}
+template <int P, int SB>
+__device__ __forceinline__ void hop_halo_bwd(cx<typename PT<P>::real> acc[12], const HopParams& hp, int s, int64_t f,
+                                             bool flip) {
+    using real = typename PT<P>::real;
+    const cx<real>* gb = static_cast<const cx<real>*>(hp.halo_bwd) + (int64_t)s * 6 * hp.face;
+    cx<real> g[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] = flip ? -gb[k * hp.face + f] : gb[k * hp.face + f];
+    reconstruct<3, SB>(acc, g);
+}
+
+template <int P, bool DAG, int MODE, bool DD = false>
 __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::value) k_hop(HopParams hp) {
     using real = typename PT<P>::real;
     int s, tile;
@@ -369,21 +407,34 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     for (int k = 0; k < 12; ++k) acc[k] = mkc<real>(0, 0);
 
     constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma (backward: 1 - SF gamma)
+    // decomposition in x4: face sites take their t-direction terms from the
+    // face buffers (the local neighbour loads there read valid memory of this
+    // domain and are not used)
+    const bool top = DD && x4 == g.L[3] - 1, bot = DD && x4 == 0;
+    const int64_t fidx = DD ? (int64_t)i - (int64_t)g.Lh * g.L[1] * g.L[2] * x4 : 0;
     if (HopPrefetch<P>::value) {
         Raw<P> cur, nxt;
         load_raw(cur, in, jn[0], d.U[p][0], ju[0]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if (k < 7) load_raw(nxt, in, jn[k + 1], d.U[((k + 1) & 1) ? q : p][(k + 1) >> 1], ju[k + 1]);
-            hop_term_d<P, SF>(k, acc, cur, flip[k]);
+            if (DD && k == 6 && top) hop_halo_fwd<P, SF>(acc, hp, s, fidx, d.U[p][3], i, hp.flip_top != 0);
+            else if (DD && k == 7 && bot) hop_halo_bwd<P, -SF>(acc, hp, s, fidx, hp.flip_bot != 0);
+            else hop_term_d<P, SF>(k, acc, cur, flip[k]);
             if (k < 7) cur = nxt;
         }
     } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            Raw<P> cur;
-            load_raw(cur, in, jn[k], d.U[(k & 1) ? q : p][k >> 1], ju[k]);
-            hop_term_d<P, SF>(k, acc, cur, flip[k]);
+            if (DD && k == 6 && top) {
+                hop_halo_fwd<P, SF>(acc, hp, s, fidx, d.U[p][3], i, hp.flip_top != 0);
+            } else if (DD && k == 7 && bot) {
+                hop_halo_bwd<P, -SF>(acc, hp, s, fidx, hp.flip_bot != 0);
+            } else {
+                Raw<P> cur;
+                load_raw(cur, in, jn[k], d.U[(k & 1) ? q : p][k >> 1], ju[k]);
+                hop_term_d<P, SF>(k, acc, cur, flip[k]);
+            }
         }
     }
 
@@ -504,8 +555,14 @@ double hop_bytes_per_site(int prec, int mode) {
 
 template <int P, bool DAG, int MODE>
 static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* out, char* y, cudaStream_t st,
-                     const int* done, int done_stride) {
+                     const int* done, int done_stride, const HopDD* dd = nullptr) {
     HopParams hp;
+    hp.halo_fwd = dd ? dd->fwd : nullptr;
+    hp.halo_bwd = dd ? dd->bwd : nullptr;
+    hp.halo_fwd_scale = dd ? dd->fwd_scale : nullptr;
+    hp.face = dd ? dd->face : 0;
+    hp.flip_top = dd ? dd->flip_top : 0;
+    hp.flip_bot = dd ? dd->flip_bot : 0;
     hp.done = done;
     hp.done_stride = done_stride;
     hp.sys = b.dev();
@@ -514,16 +571,22 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     hp.out = out;
     hp.y = y;
     hp.a_sign = a_sign;
-    const std::string key = "hop" + std::to_string(P) + (DAG ? "d" : "n") + std::to_string(MODE) + "_" +
-                            std::to_string(b.Vh_max) + "x" + std::to_string(b.nsys()) + (b.uniform ? "u" : "r");
+    const std::string key = "hop" + std::to_string(P) + (DAG ? "d" : "n") + std::to_string(MODE) + (dd ? "dd" : "") +
+                            "_" + std::to_string(b.Vh_max) + "x" + std::to_string(b.nsys()) + (b.uniform ? "u" : "r");
     const bool may_tune = out != y && out != in;
     auto run = [&](int B) {
         int nb = 0;
         hp.map = block_map(b, B, nb);
+        if constexpr (P != P64S) {
+            if (dd) {
+                k_hop<P, DAG, MODE, true><<<nb, B, 0, st>>>(hp);
+                return;
+            }
+        }
         k_hop<P, DAG, MODE><<<nb, B, 0, st>>>(hp);
     };
     // right-hand sides of one gauge field can share each link load in registers
-    bool shared = b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
+    bool shared = !dd && b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
     for (int s = 1; shared && s < b.nsys(); ++s) shared = b.sys[s].U[0][0].data == b.sys[0].U[0][0].data;
     auto run_multi = [&](int R, int B) {
         BlockMap m;
@@ -599,33 +662,106 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
 
 template <int P, bool DAG>
 static void launch_mode(const Batch& b, int parity, int mode, double a_sign, char* in, char* out, char* y,
-                        cudaStream_t st, const int* dn, int ds) {
+                        cudaStream_t st, const int* dn, int ds, const HopDD* dd) {
     switch (mode) {
-        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st, dn, ds); break;
-        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds); break;
-        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds); break;
-        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st, dn, ds); break;
-        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds); break;
+        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
+        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
+        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
+        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
+        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
         default: throw Error(BPP_ERR_INVALID_ARG, "bad hopping mode");
+    }
+}
+
+static void hop_any(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
+                    cudaStream_t st, const int* dn, int ds, const HopDD* dd) {
+    BPP_REQUIRE(in != out, BPP_ERR_INVALID_ARG, "hopping term: output aliases input");
+    if (b.prec == P64) {
+        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
+            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+    } else if (b.prec == P32) {
+        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
+            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+    } else if (b.prec == P64S) {
+        BPP_REQUIRE(!dd, BPP_ERR_UNSUPPORTED, "the decomposed hopping term takes FP64, FP32 or FP16");
+        dag ? launch_mode<P64S, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
+            : launch_mode<P64S, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+    } else {
+        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
+            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
     }
 }
 
 void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
          cudaStream_t st, const int* dn, int ds) {
-    BPP_REQUIRE(in != out, BPP_ERR_INVALID_ARG, "hopping term: output aliases input");
-    if (b.prec == P64) {
-        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
-            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
-    } else if (b.prec == P32) {
-        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
-            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
-    } else if (b.prec == P64S) {
-        dag ? launch_mode<P64S, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
-            : launch_mode<P64S, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
+    hop_any(b, parity, dag, mode, a_sign, in, out, y, st, dn, ds, nullptr);
+}
+
+void hop_dd(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
+            const HopDD& dd, cudaStream_t st, const int* dn, int ds) {
+    hop_any(b, parity, dag, mode, a_sign, in, out, y, st, dn, ds, &dd);
+}
+
+// One thread per face site of both faces of the input field's parity q:
+// the bottom face (x4 = 0) sends (1 + SF gamma_4) psi down, the top face
+// (x4 = L4 - 1) sends U_4(x)^dag (1 - SF gamma_4) psi up (the arithmetic of
+// hop_term for the corresponding hops of the neighbouring domains).
+template <int P, bool DAG>
+__global__ void k_dd_pack(const SysDesc* sys, BlockMap map, int q, const char* in, void* send_down,
+                          float* send_down_scale, void* send_up, int64_t face) {
+    using real = typename PT<P>::real;
+    int s, tile;
+    map_block(map, s, tile);
+    const SysDesc& d = sys[s];
+    const int64_t t = (int64_t)tile * blockDim.x + threadIdx.x;
+    if (t >= 2 * face) return;
+    const bool up = t >= face;
+    const int64_t f = up ? t - face : t;
+    const int64_t i = up ? face * (d.g.L[3] - 1) + f : f;
+    constexpr int SF = DAG ? +1 : -1;
+    Raw<P> raw;
+    load_raw(raw, sys_view<P>(const_cast<char*>(in), d), i, d.U[q][3], i);
+    cx<real> psi[12], u[9], h[6];
+    decode(raw, psi, u);
+    if (!up) {
+        project<3, SF>(psi, h);
+        cx<real>* o = static_cast<cx<real>*>(send_down) + (int64_t)s * 6 * face;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k * face + f] = h[k];
+        if (P == P16) send_down_scale[(int64_t)s * face + f] = __ldg(sys_view<P>(const_cast<char*>(in), d).scale + i);
     } else {
-        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds)
-            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds);
+        cx<real> gg[6];
+        project<3, -SF>(psi, h);
+        link_mul<true>(u, h, gg);
+        cx<real>* o = static_cast<cx<real>*>(send_up) + (int64_t)s * 6 * face;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k * face + f] = gg[k];
     }
+}
+
+void dd_pack(const Batch& b, int in_parity, int dag, const char* in, void* send_down, float* send_down_scale,
+             void* send_up, int64_t face, cudaStream_t st) {
+    const int B = 128;
+    BlockMap m;
+    m.nsys = b.nsys();
+    m.uniform = 1;
+    m.tiles_per_sys = (int)((2 * face + B - 1) / B);
+    for (int t = 0; t <= MAXSYS; ++t) m.tile_start[t] = 0;
+    const int nb = m.tiles_per_sys * m.nsys;
+    // per face site: the spinor read, the link read on the top face, 6
+    // complex of face buffer written
+    const double csize = b.prec == P64 ? 16.0 : 8.0;
+    const double bytes = (double)b.nsys() * face * (2.0 * spinor_bytes(b.prec) + link_bytes(b.prec) + 2 * 6 * csize);
+    ProfScope prof(PROF_OUTER, bytes, st);
+    if (b.prec == P64) dag ? k_dd_pack<P64, true><<<nb, B, 0, st>>>(b.dev(), m, in_parity, in, send_down, send_down_scale, send_up, face)
+                           : k_dd_pack<P64, false><<<nb, B, 0, st>>>(b.dev(), m, in_parity, in, send_down, send_down_scale, send_up, face);
+    else if (b.prec == P32) dag ? k_dd_pack<P32, true><<<nb, B, 0, st>>>(b.dev(), m, in_parity, in, send_down, send_down_scale, send_up, face)
+                                : k_dd_pack<P32, false><<<nb, B, 0, st>>>(b.dev(), m, in_parity, in, send_down, send_down_scale, send_up, face);
+    else if (b.prec == P16) dag ? k_dd_pack<P16, true><<<nb, B, 0, st>>>(b.dev(), m, in_parity, in, send_down, send_down_scale, send_up, face)
+                                : k_dd_pack<P16, false><<<nb, B, 0, st>>>(b.dev(), m, in_parity, in, send_down, send_down_scale, send_up, face);
+    else throw Error(BPP_ERR_UNSUPPORTED, "the decomposed hopping term takes FP64, FP32 or FP16");
+    count_launch();
+    BPP_CHECK_LAUNCH();
 }
 
 }  // namespace bpp
@@ -647,6 +783,10 @@ void hop_fixed(int prec, const SysDesc* dsys, int nsys, int Vh, int parity, int 
     hp.a_sign = a_sign;
     hp.done = nullptr;
     hp.done_stride = 0;
+    hp.halo_fwd = hp.halo_bwd = nullptr;
+    hp.halo_fwd_scale = nullptr;
+    hp.face = 0;
+    hp.flip_top = hp.flip_bot = 0;
     hp.map.nsys = nsys;
     hp.map.uniform = 1;
     hp.map.tiles_per_sys = (Vh + B - 1) / B;

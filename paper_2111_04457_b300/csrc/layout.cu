@@ -78,13 +78,14 @@ __global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, con
 }
 
 // Half fields: canonical [nsys][Vh][4][3] with system s at offset s*Vh*12.
+// cstride: elements of TC between systems (< 0: Vh * 12, consecutive fields).
 template <int P, class TC>
-__global__ void k_half_to_int(const SysDesc* sys, const TC* __restrict__ canon, char* out) {
+__global__ void k_half_to_int(const SysDesc* sys, const TC* __restrict__ canon, char* out, int64_t cstride) {
     using real = typename PT<P>::real;
     const SysDesc& d = sys[blockIdx.y];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.g.Vh) return;
-    const TC* src = canon + ((int64_t)blockIdx.y * d.g.Vh + i) * 12;
+    const TC* src = canon + (int64_t)blockIdx.y * (cstride < 0 ? (int64_t)d.g.Vh * 12 : cstride) + i * 12;
     cx<real> v[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = from_canon<TC, real>(src[k]);
@@ -92,14 +93,14 @@ __global__ void k_half_to_int(const SysDesc* sys, const TC* __restrict__ canon, 
 }
 
 template <int P, class TC>
-__global__ void k_int_to_half(const SysDesc* sys, const char* in, TC* canon) {
+__global__ void k_int_to_half(const SysDesc* sys, const char* in, TC* canon, int64_t cstride) {
     using real = typename PT<P>::real;
     const SysDesc& d = sys[blockIdx.y];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.g.Vh) return;
     cx<real> v[12];
     Access<P>::load_spinor(sys_view<P>(const_cast<char*>(in), d), i, v);
-    TC* dst = canon + ((int64_t)blockIdx.y * d.g.Vh + i) * 12;
+    TC* dst = canon + (int64_t)blockIdx.y * (cstride < 0 ? (int64_t)d.g.Vh * 12 : cstride) + i * 12;
 #pragma unroll
     for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>(v[k]);
 }
@@ -142,25 +143,25 @@ void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char
     BPP_CHECK_LAUNCH();
 }
 
-void half_to_int(const Batch& b, const void* canon, int canon_f64, char* out, cudaStream_t st) {
+void half_to_int(const Batch& b, const void* canon, int canon_f64, char* out, cudaStream_t st, int64_t cstride) {
     const int B = 256;
     dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
     ProfScope prof(PROF_LAYOUT, b.sites() * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
-        if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(b.dev(), static_cast<const double2*>(canon), out);
-        else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(b.dev(), static_cast<const float2*>(canon), out);
+        if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(b.dev(), static_cast<const double2*>(canon), out, cstride);
+        else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(b.dev(), static_cast<const float2*>(canon), out, cstride);
     });
     count_launch();
     BPP_CHECK_LAUNCH();
 }
 
-void int_to_half(const Batch& b, const char* in, void* canon, int canon_f64, cudaStream_t st) {
+void int_to_half(const Batch& b, const char* in, void* canon, int canon_f64, cudaStream_t st, int64_t cstride) {
     const int B = 256;
     dim3 grid((unsigned)((b.Vh_max + B - 1) / B), b.nsys());
     ProfScope prof(PROF_LAYOUT, b.sites() * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
-        if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<double2*>(canon));
-        else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<float2*>(canon));
+        if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<double2*>(canon), cstride);
+        else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(b.dev(), in, static_cast<float2*>(canon), cstride);
     });
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -177,8 +178,8 @@ void half_to_int_fixed(int prec, const SysDesc* dsys, int nsys, int Vh, const vo
     const int B = 256;
     dim3 grid((unsigned)((Vh + B - 1) / B), nsys);
     BPP_PREC_DISPATCH(prec, {
-        if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(dsys, static_cast<const double2*>(canon), out);
-        else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(dsys, static_cast<const float2*>(canon), out);
+        if (canon_f64) k_half_to_int<PP, double2><<<grid, B, 0, st>>>(dsys, static_cast<const double2*>(canon), out, -1);
+        else k_half_to_int<PP, float2><<<grid, B, 0, st>>>(dsys, static_cast<const float2*>(canon), out, -1);
     });
     count_launch();
 }
@@ -188,8 +189,8 @@ void int_to_half_fixed(int prec, const SysDesc* dsys, int nsys, int Vh, const ch
     const int B = 256;
     dim3 grid((unsigned)((Vh + B - 1) / B), nsys);
     BPP_PREC_DISPATCH(prec, {
-        if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(dsys, in, static_cast<double2*>(canon));
-        else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(dsys, in, static_cast<float2*>(canon));
+        if (canon_f64) k_int_to_half<PP, double2><<<grid, B, 0, st>>>(dsys, in, static_cast<double2*>(canon), -1);
+        else k_int_to_half<PP, float2><<<grid, B, 0, st>>>(dsys, in, static_cast<float2*>(canon), -1);
     });
     count_launch();
 }
