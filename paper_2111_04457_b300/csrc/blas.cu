@@ -406,8 +406,11 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_down(OuterParams op) {
 __device__ __forceinline__ df64 to_df(float v) { return df64(v, 0.f); }
 __device__ __forceinline__ df64 to_df(double v) { return df64(v); }
 
+template <int P> struct OuterAccMinBlocks { static constexpr int value = 4; };
+template <> struct OuterAccMinBlocks<P64> { static constexpr int value = 2; };
+
 template <int P>
-__global__ void __launch_bounds__(BLAS_B) k_outer_acc(OuterParams op) {
+__global__ void __launch_bounds__(BLAS_B, OuterAccMinBlocks<P>::value) k_outer_acc(OuterParams op) {
     using real = typename PT<P>::real;
     int s, tile;
     map_block(op.map, s, tile);
@@ -415,25 +418,28 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_acc(OuterParams op) {
     const int i = tile * blockDim.x + threadIdx.x;
     if (i >= d.g.Vh) return;
     const double sc = op.sc[s].scale;
-    cx<double> x[12];
     cx<real> e[12];
-    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, x);
     Access<P>::load_spinor(sys_view<P>(op.b, op.sP[s]), i, e);
+    // component by component (no whole FP64 or split spinor held in registers)
+    double2* xp = reinterpret_cast<double2*>(op.a + d.vec_off);
+    float4* xsp = op.c ? reinterpret_cast<float4*>(op.c + d.vec_off) : nullptr;
+    const df64 scd(sc);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) x[k] = x[k] + sc * mkc<double>((double)e[k].r, (double)e[k].i);
-    Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, x);
-    if (op.c) {
-        // the split copy takes the same update in double-float arithmetic (no
-        // FP64 conversions); it tracks x to ~1e-14 and only feeds the defects
-        cx<df64> xs[12];
-        Access<P64S>::load_spinor(sys_view<P64S>(op.c, d), i, xs);
-        const df64 scd(sc);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            xs[k].r = fma(scd, to_df(e[k].r), xs[k].r);
-            xs[k].i = fma(scd, to_df(e[k].i), xs[k].i);
+    for (int k = 0; k < 12; ++k) {
+        const int64_t j = k * d.stride + i;
+        double2 xv = xp[j];
+        xv.x = fma(sc, (double)e[k].r, xv.x);
+        xv.y = fma(sc, (double)e[k].i, xv.y);
+        xp[j] = xv;
+        if (xsp) {
+            // the split copy takes the same update in double-float arithmetic
+            // (no FP64 conversions); it tracks x to ~1e-14 and only feeds the
+            // defects
+            const float4 v = xsp[j];
+            const df64 r = normalized(fma(scd, to_df(e[k].r), df64(v.x, v.y)));
+            const df64 m = normalized(fma(scd, to_df(e[k].i), df64(v.z, v.w)));
+            xsp[j] = make_float4(r.hi, r.lo, m.hi, m.lo);
         }
-        Access<P64S>::store_spinor(sys_view<P64S>(op.c, d), i, xs);
     }
 }
 
@@ -449,17 +455,27 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
     const int i = tile * blockDim.x + threadIdx.x;
     float red[4] = {0.f, 0.f, 0.f, 0.f};
     if (i < d.g.Vh) {
-        cx<df64> bh[12], m[12];
-        Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, bh);
-        if (op.b) {
-            Access<P64S>::load_spinor(sys_view<P64S>(op.b, d), i, m);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) bh[k] = bh[k] - m[k];
-        }
-        Access<P64S>::store_spinor(sys_view<P64S>(op.c, d), i, bh);
+        // component by component (no whole split spinor held in registers)
+        const float4* pa = reinterpret_cast<const float4*>(op.a + d.vec_off);
+        const float4* pb = op.b ? reinterpret_cast<const float4*>(op.b + d.vec_off) : nullptr;
+        float4* pc = reinterpret_cast<float4*>(op.c + d.vec_off);
         float n = 0.f;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) { n = fmaf(bh[k].r.hi, bh[k].r.hi, n); n = fmaf(bh[k].i.hi, bh[k].i.hi, n); }
+        for (int k = 0; k < 12; ++k) {
+            const int64_t j = k * d.stride + i;
+            const float4 va = pa[j];
+            df64 r(va.x, va.y), m(va.z, va.w);
+            if (pb) {
+                const float4 vb = pb[j];
+                r = r - df64(vb.x, vb.y);
+                m = m - df64(vb.z, vb.w);
+            }
+            r = normalized(r);
+            m = normalized(m);
+            pc[j] = make_float4(r.hi, r.lo, m.hi, m.lo);
+            n = fmaf(r.hi, r.hi, n);
+            n = fmaf(m.hi, m.hi, n);
+        }
         red[0] = n;
     }
     double tot[4];

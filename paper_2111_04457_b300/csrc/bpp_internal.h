@@ -120,6 +120,10 @@ template <class T> __device__ __forceinline__ void cfma(cx<T>& a, cx<T> b, cx<T>
     a.r = fma(b.r, c.r, a.r); a.r = fma(-b.i, c.i, a.r);
     a.i = fma(b.r, c.i, a.i); a.i = fma(b.i, c.r, a.i);
 }
+// a * x + y for a real a (one rounding per component)
+template <class T> __device__ __forceinline__ cx<T> cxfma(T a, cx<T> x, cx<T> y) {
+    return mkc(fma(a, x.r, y.r), fma(a, x.i, y.i));
+}
 // a += conj(b) * c
 template <class T> __device__ __forceinline__ void cfmac(cx<T>& a, cx<T> b, cx<T> c) {
     a.r = fma(b.r, c.r, a.r); a.r = fma(b.i, c.i, a.r);

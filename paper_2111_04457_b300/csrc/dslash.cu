@@ -438,10 +438,9 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
         }
     }
 
+    // v = a hop (+ y, or + A y): the xpay forms as one fused multiply-add
     const real a = (real)(hp.a_sign * d.kappa);
     cx<real> v[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = a * acc[k];
     if (MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY || MODE == HOP_INV_XPAY) {
         cx<real> y[12];
         Access<P>::load_spinor(sys_view<P>(hp.y, d), i, y);
@@ -449,11 +448,14 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
             cx<real> ay[12];
             clover_apply_site<P>(d.A[p], i, y, ay);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) v[k] = v[k] + ay[k];
+            for (int k = 0; k < 12; ++k) v[k] = cxfma(a, acc[k], ay[k]);
         } else {
 #pragma unroll
-            for (int k = 0; k < 12; ++k) v[k] = v[k] + y[k];
+            for (int k = 0; k < 12; ++k) v[k] = cxfma(a, acc[k], y[k]);
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = a * acc[k];
     }
     if (MODE == HOP_INV || MODE == HOP_INV_XPAY) {
         cx<real> w[12];
@@ -517,8 +519,6 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
         const SysDesc& d = hp.sys[s0 + r];
         const real a = (real)(hp.a_sign * d.kappa);
         cx<real> v[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = a * acc[r][k];
         if (MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY || MODE == HOP_INV_XPAY) {
             cx<real> y[12];
             Access<P>::load_spinor(sys_view<P>(hp.y, d), i, y);
@@ -526,11 +526,14 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
                 cx<real> ay[12];
                 clover_apply_site<P>(d.A[p], i, y, ay);
 #pragma unroll
-                for (int k = 0; k < 12; ++k) v[k] = v[k] + ay[k];
+                for (int k = 0; k < 12; ++k) v[k] = cxfma(a, acc[r][k], ay[k]);
             } else {
 #pragma unroll
-                for (int k = 0; k < 12; ++k) v[k] = v[k] + y[k];
+                for (int k = 0; k < 12; ++k) v[k] = cxfma(a, acc[r][k], y[k]);
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = a * acc[r][k];
         }
         if (MODE == HOP_INV || MODE == HOP_INV_XPAY) {
             cx<real> w[12];
