@@ -342,6 +342,70 @@ int bpp_dd_schur_apply(bpp_dd dd, const void* in, void* out, double kappa, int d
 int bpp_dd_solve(bpp_dd dd, const void* b, void* x, double kappa, double tol, int nrhs, const bpp_solve_opts* opts,
                  bpp_solve_stats* stats, bpp_stream stream);
 
+/* ---- Multigrid (the multi-grid solver of Sec. 1 and Sec. 4), two levels,
+ * for the full-lattice matrix D of Eq. (1) (Wilson or Wilson-clover):
+ *   prolongator P: the lattice is cut into blocks of block[0..3] sites; on
+ *     every block and chirality (spins 0,1 / spins 2,3) six near-null vectors
+ *     restricted there are orthonormalised (Gram-Schmidt, fixed order), so a
+ *     block carries 12 coarse degrees of freedom (chirality-major, then
+ *     vector); restriction is P^dag;
+ *   coarse operator D_c = P^dag D P: a nearest-neighbour stencil on the block
+ *     lattice (a self term and one term per direction and sense, 12x12 each);
+ *   V-cycle: nu_pre minimal-residual steps on D, restriction, BiCGStab on D_c
+ *     to coarse_tol (at most coarse_maxiter iterations), prolongation, the
+ *     residual recomputed, nu_post minimal-residual steps;
+ *   solve: flexible GCR(gcr_restart) on D preconditioned by the V-cycle in
+ *     FP32, inside FP64 defect correction until ||b - D x|| / ||b|| <= tol.
+ * The preconditioner works in FP32. */
+typedef struct bpp_mg_s* bpp_mg;
+
+typedef struct {
+    int nu_pre, nu_post;   /* minimal-residual smoothing steps before / after the coarse correction */
+    double coarse_tol;     /* relative residual of the coarse BiCGStab */
+    int coarse_maxiter;    /* iteration cap of the coarse BiCGStab */
+    int gcr_restart;       /* GCR directions kept before a restart (1..64) */
+    double setup_tol;      /* relative residual of the solves that improve the near-null vectors */
+} bpp_mg_params;
+
+/* Defaults: nu_pre 2, nu_post 2, coarse_tol 0.05, coarse_maxiter 100,
+ * gcr_restart 12, setup_tol 0.05. */
+void bpp_mg_params_default(bpp_mg_params* p);
+
+/* Builds the prolongator and the coarse operator for D on gauge U (kappa,
+ * csw; csw != 0 requires bpp_clover_build with the same kappa and csw).
+ * vectors: six canonical complex128 full fields [6][V][4][3] (device or host),
+ * the near-null vectors, or the starting vectors when refine > 0: each of the
+ * refine passes replaces them by approximate solutions of D v' = v (mixed
+ * precision, relative residual setup_tol), one inverse-iteration step.  The
+ * library draws no random numbers.  block: extents dividing L, 32..256 sites
+ * per block (a multiple of 32).  params: NULL for the defaults.  U must
+ * outlive the handle.  Synchronises `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int bpp_mg_create(bpp_gauge U, double kappa, double csw, const int block[4], const void* vectors, int refine,
+                  const bpp_mg_params* params, bpp_stream stream, bpp_mg* out);
+int bpp_mg_destroy(bpp_mg mg);
+
+/* The multigrid operators on canonical complex64 fields (device memory), for
+ * checking and for use as building blocks:
+ *   BPP_MG_PROLONG:  out = P in,     in [nrhs][Vc][12], out [nrhs][V][4][3]
+ *   BPP_MG_RESTRICT: out = P^dag in, in [nrhs][V][4][3], out [nrhs][Vc][12]
+ *   BPP_MG_COARSE:   out = D_c in,   coarse fields
+ *   BPP_MG_VCYCLE:   out = M in (the preconditioner), full fields
+ * Coarse index: block b = b0 + Lc0 (b1 + Lc1 (b2 + Lc2 b3)), Lc = L / block;
+ * component chirality * 6 + vector.  Synchronises `stream`. */
+enum { BPP_MG_PROLONG = 0, BPP_MG_RESTRICT = 1, BPP_MG_COARSE = 2, BPP_MG_VCYCLE = 3 };
+int bpp_mg_apply(bpp_mg mg, int op, const void* in, void* out, int nrhs, bpp_stream stream);
+
+/* Solves D x = b (opts->dagger: D^dag x = b, through gamma5-hermiticity) with
+ * the multigrid-preconditioned GCR under FP64 defect correction;
+ * opts->inner_tol (<= 0: 1e-6) is the relative reduction per inner solve,
+ * opts->max_inner caps the GCR iterations of one inner solve, opts->max_outer
+ * the corrections.  b, x: device complex128 [nrhs][V][4][3].  stats as
+ * bpp_solve (inner_iters counts preconditioned GCR iterations).
+ * Synchronises `stream`.  Errors: as bpp_solve. */
+int bpp_mg_solve(bpp_mg mg, const void* b, void* x, double tol, int nrhs, const bpp_solve_opts* opts,
+                 bpp_solve_stats* stats, bpp_stream stream);
+
 /* Number of kernels this library has launched since load (or since the last
  * reset when reset != 0); graph launches count each kernel node they run. */
 int64_t bpp_launch_count(int reset);

@@ -468,3 +468,47 @@ def free_field_solve_dft(b, kappa, L, bc=DEFAULT_BC):
     out = np.einsum("za,xyawsc->xyzwsc", Ei[1], out)
     out = np.einsum("wa,xyzasc->xyzwsc", Ei[0], out)
     return out.reshape(volume(L), 4, 3)
+
+
+# ---------------------------------------------------------------------------
+# Two-level aggregation multigrid (the multi-grid solver named in Sec. 1 and
+# Sec. 4; the paper gives no construction, the reading is the standard
+# aggregation with chirality-split blocks): the prolongator and the Galerkin
+# coarse operator, by their definitions, as dense matrices (small lattices).
+def mg_block_index(L, block):
+    """Block index of every lexicographic site, b0 + Lc0 (b1 + Lc1 (b2 + Lc2 b3)),
+    and the block-lattice extents Lc."""
+    Lc = [L[m] // block[m] for m in range(4)]
+    b = coords(L) // np.asarray(block)
+    return b[:, 0] + Lc[0] * (b[:, 1] + Lc[1] * (b[:, 2] + Lc[2] * b[:, 3])), Lc
+
+
+def mg_prolongator(vecs, L, block):
+    """P as a dense (12 V) x (12 Vc) matrix.  Column (B, 6 chi + k) is the k-th
+    vector of the Gram-Schmidt orthonormalisation, in the order k = 0..5, of the
+    six vectors vecs[k] restricted to block B and chirality chi (spins 2 chi,
+    2 chi + 1).  Gram-Schmidt in order is the QR factorisation whose R has a
+    positive real diagonal."""
+    vecs = np.asarray(vecs)
+    V = volume(L)
+    bidx, Lc = mg_block_index(L, block)
+    Vc = int(np.prod(Lc))
+    P = np.zeros((V, 4, 3, Vc, 12), dtype=np.complex128)
+    for B in range(Vc):
+        sites = np.flatnonzero(bidx == B)
+        for chi in range(2):
+            A = vecs[:, sites][:, :, 2 * chi:2 * chi + 2, :].reshape(6, -1).T
+            Q, R = np.linalg.qr(A)
+            d = np.diag(R)
+            Q = Q * (d / np.abs(d))[None, :]
+            P[sites, 2 * chi:2 * chi + 2, :, B, 6 * chi:6 * chi + 6] = Q.reshape(len(sites), 2, 3, 6)
+    return P.reshape(V * 12, Vc * 12)
+
+
+def mg_coarse_operator(U, kappa, L, P, bc=DEFAULT_BC, F=None):
+    """D_c = P^dag D P with D of Eq. (1) applied to every column of P."""
+    V = volume(L)
+    DP = np.empty_like(P)
+    for j in range(P.shape[1]):
+        DP[:, j] = apply_D(U, P[:, j].reshape(V, 4, 3), kappa, L, bc, F).reshape(-1)
+    return P.conj().T @ DP

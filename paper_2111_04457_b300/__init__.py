@@ -90,6 +90,11 @@ _SIGS = {
     "bpp_dd_dslash": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
     "bpp_dd_schur_apply": ([_p, _p, _p, _d, _i, _i, _i, _p], _i),
     "bpp_dd_solve": ([_p, _p, _p, _d, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
+    "bpp_mg_params_default": ([_p], None),
+    "bpp_mg_create": ([_p, _d, _d, ctypes.POINTER(_i), _p, _i, _p, _p, ctypes.POINTER(_p)], _i),
+    "bpp_mg_destroy": ([_p], _i),
+    "bpp_mg_apply": ([_p, _i, _p, _p, _i, _p], _i),
+    "bpp_mg_solve": ([_p, _p, _p, _d, _i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _p], _i),
     "bpp_launch_count": ([_i], _i64),
     "bpp_prof_enable": ([_i], _i),
     "bpp_prof_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), ctypes.POINTER(_d), _i], _i),
@@ -507,6 +512,107 @@ class DomainDecomposition:
     def destroy(self):
         if getattr(self, "_h", None) is not None:
             _lib.bpp_dd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("coarse_tol", ctypes.c_double),
+                ("coarse_maxiter", ctypes.c_int), ("gcr_restart", ctypes.c_int), ("setup_tol", ctypes.c_double)]
+
+
+MG_PROLONG, MG_RESTRICT, MG_COARSE, MG_VCYCLE = 0, 1, 2, 3
+
+
+def mg_params(**kw) -> MGParams:
+    p = MGParams()
+    _lib.bpp_mg_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Multigrid:
+    """Two-level aggregation multigrid for the full-lattice D (bpp_mg_*).
+
+    vectors: complex128 [6][V][4][3] near-null (or starting) vectors, CUDA or
+    CPU; refine: inverse-iteration passes applied to them; block: the
+    aggregate extents.  The gauge g (with its clover term for csw != 0) must
+    outlive this object."""
+
+    def __init__(self, g: Gauge, kappa: float, vectors: torch.Tensor, block, csw: float = 0.0, refine: int = 0,
+                 params: MGParams = None, stream=None):
+        if vectors.dtype != torch.complex128 or tuple(vectors.shape) != (6, g.lattice.V, 4, 3):
+            raise ValueError("vectors must be complex128 of shape (6, V, 4, 3)")
+        vectors = vectors.contiguous()
+        self.gauge = g
+        self.kappa, self.csw = float(kappa), float(csw)
+        self.block = tuple(int(b) for b in block)
+        self.Lc = tuple(g.lattice.L[m] // self.block[m] for m in range(4))
+        self.Vc = self.Lc[0] * self.Lc[1] * self.Lc[2] * self.Lc[3]
+        h = _p()
+        bs = (ctypes.c_int * 4)(*self.block)
+        _check(_lib.bpp_mg_create(g.handle, self.kappa, self.csw, bs, _ptr(vectors), int(refine),
+                                  ctypes.byref(params) if params is not None else None, _stream(stream),
+                                  ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("multigrid handle destroyed")
+        return self._h
+
+    def _apply(self, op, x, out_shape, stream=None):
+        _cuda(x, "input")
+        if x.dtype != torch.complex64:
+            raise ValueError("multigrid operators take complex64 fields")
+        x = x.contiguous()
+        per = 12 * (self.Vc if op in (MG_PROLONG, MG_COARSE) else self.gauge.lattice.V)
+        n = _nrhs(x, per)
+        out = torch.empty((n,) + out_shape, dtype=torch.complex64, device=x.device)
+        _check(_lib.bpp_mg_apply(self.handle, op, _ptr(x), _ptr(out), n, _stream(stream)))
+        return out
+
+    def prolong(self, c, stream=None):
+        """P c: coarse [nrhs][Vc][12] -> full [nrhs][V][4][3]."""
+        return self._apply(MG_PROLONG, c, (self.gauge.lattice.V, 4, 3), stream)
+
+    def restrict(self, f, stream=None):
+        """P^dag f: full [nrhs][V][4][3] -> coarse [nrhs][Vc][12]."""
+        return self._apply(MG_RESTRICT, f, (self.Vc, 12), stream)
+
+    def coarse(self, c, stream=None):
+        """D_c c on coarse fields."""
+        return self._apply(MG_COARSE, c, (self.Vc, 12), stream)
+
+    def vcycle(self, f, stream=None):
+        """M f (the preconditioner) on full fields."""
+        return self._apply(MG_VCYCLE, f, (self.gauge.lattice.V, 4, 3), stream)
+
+    def solve(self, b: torch.Tensor, tol: float = 1e-10, opts: SolveOpts = None, stream=None, raise_on_fail=True):
+        _cuda(b, "b")
+        if b.dtype != torch.complex128:
+            raise ValueError("b must be complex128")
+        b = b.contiguous()
+        n = _nrhs(b, 12 * self.gauge.lattice.V)
+        x = torch.empty_like(b)
+        o = opts if opts is not None else solve_opts(max_inner=200)
+        st = (SolveStats * n)()
+        rc = _lib.bpp_mg_solve(self.handle, _ptr(b), _ptr(x), float(tol), n, ctypes.byref(o), st, _stream(stream))
+        stats = [s.as_dict() for s in st]
+        if raise_on_fail:
+            _check(rc)
+        return x, stats
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.bpp_mg_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -10,6 +10,7 @@
 #include "kernels.h"
 #include "solver.h"
 #include "dd.h"
+#include "mg.h"
 
 namespace bpp {
 int prof_enable(int on);
@@ -446,6 +447,57 @@ int bpp_dd_solve(bpp_dd dd, const void* b, void* x, double kappa, double tol, in
         if (opts) o = *opts;
         const int rc = dd_solve(dd, b, x, kappa, tol, nrhs, o, stats, reinterpret_cast<cudaStream_t>(stream));
         if (rc != BPP_OK) return fail(rc, "bpp_dd_solve: a right-hand side did not reach the tolerance (see stats)");
+        return BPP_OK;
+    });
+}
+
+void bpp_mg_params_default(bpp_mg_params* p) {
+    if (!p) return;
+    p->nu_pre = 2;
+    p->nu_post = 2;
+    p->coarse_tol = 0.05;
+    p->coarse_maxiter = 100;
+    p->gcr_restart = 12;
+    p->setup_tol = 0.05;
+}
+
+int bpp_mg_create(bpp_gauge U, double kappa, double csw, const int block[4], const void* vectors, int refine,
+                  const bpp_mg_params* params, bpp_stream stream, bpp_mg* out) {
+    return guard("bpp_mg_create", [&]() -> int {
+        check_gauge(U);
+        BPP_REQUIRE(std::isfinite(kappa) && std::isfinite(csw), BPP_ERR_INVALID_ARG, "kappa and csw must be finite");
+        BPP_REQUIRE(refine >= 0 && refine <= 8, BPP_ERR_INVALID_ARG, "refine must be 0..8");
+        mg_create(U, kappa, csw, block, vectors, refine, params, reinterpret_cast<cudaStream_t>(stream), out);
+        return BPP_OK;
+    });
+}
+
+int bpp_mg_destroy(bpp_mg mg) {
+    return guard("bpp_mg_destroy", [&]() -> int {
+        mg_destroy(mg);
+        return BPP_OK;
+    });
+}
+
+int bpp_mg_apply(bpp_mg mg, int op, const void* in, void* out, int nrhs, bpp_stream stream) {
+    return guard("bpp_mg_apply", [&]() -> int {
+        BPP_REQUIRE(in && out && in != out && is_device_ptr(in) && is_device_ptr(out), BPP_ERR_INVALID_ARG,
+                    "in and out must be distinct device buffers");
+        mg_apply_op(mg, op, in, out, nrhs, reinterpret_cast<cudaStream_t>(stream));
+        return BPP_OK;
+    });
+}
+
+int bpp_mg_solve(bpp_mg mg, const void* b, void* x, double tol, int nrhs, const bpp_solve_opts* opts,
+                 bpp_solve_stats* stats, bpp_stream stream) {
+    return guard("bpp_mg_solve", [&]() -> int {
+        BPP_REQUIRE(b && x && is_device_ptr(b) && is_device_ptr(x), BPP_ERR_INVALID_ARG, "b and x must be device memory");
+        bpp_solve_opts o;
+        bpp_solve_opts_default(&o);
+        o.max_inner = 200;
+        if (opts) o = *opts;
+        const int rc = mg_solve(mg, b, x, tol, nrhs, o, stats, reinterpret_cast<cudaStream_t>(stream));
+        if (rc != BPP_OK) return fail(rc, "bpp_mg_solve: a right-hand side did not reach the tolerance (see stats)");
         return BPP_OK;
     });
 }

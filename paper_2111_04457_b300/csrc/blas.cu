@@ -145,6 +145,18 @@ __device__ __forceinline__ void blas_site(const BlasParams& bp, const SysDesc& d
         A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
         A::load_spinor(sys_view<P>(bp.v.r, d), i, b);
         red[0] += norm12(a) + norm12(b);
+    } else if (OP == B_MR) {
+        const cx<real> omr = mkc<real>((real)om.x, (real)om.y);
+        A::load_spinor(sys_view<P>(bp.v.x, d), i, a);
+        A::load_spinor(sys_view<P>(bp.v.s, d), i, b);
+        A::load_spinor(sys_view<P>(bp.v.t, d), i, c);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            cfma(a[k], omr, b[k]);
+            cfma(b[k], -omr, c[k]);
+        }
+        A::store_spinor(sys_view<P>(bp.v.x, d), i, a);
+        A::store_spinor(sys_view<P>(bp.v.s, d), i, b);
     }
 }
 
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
             if (i < d.g.Vh) blas_site<P, OP>(bp, d, i, al, om, be, red);
         }
     }
-    constexpr bool HAS_RED = OP != B_S && OP != B_P;
+    constexpr bool HAS_RED = OP != B_S && OP != B_P && OP != B_MR;
     if (!HAS_RED) return;
     if (!active) return;   // whole system inactive: every block of it returns here
     double tot[4];
@@ -284,7 +296,7 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
     bp.partials = rb.partials.as<double>();
     bp.tickets = rb.tickets.as<unsigned>();
     // vectors each op reads plus writes (its algorithmic traffic per site)
-    static const int passes[] = {5, 2, 3, 2, 7, 4, 3, 2, 1, 6, 4, 1, 2};
+    static const int passes[] = {5, 2, 3, 2, 7, 4, 3, 2, 1, 6, 4, 1, 2, 5};
     ProfScope prof(PROF_BLAS, bt.sites() * spinor_bytes(P) * passes[op], st);
     switch (op) {
         case B_INIT_BICG: k_blas<P, B_INIT_BICG><<<nb, BLAS_B, 0, st>>>(bp); break;
@@ -304,6 +316,7 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
             break;
         case B_NORM2: k_blas<P, B_NORM2><<<nb, BLAS_B, 0, st>>>(bp); break;
         case B_NORM2X2: k_blas<P, B_NORM2X2><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_MR: k_blas<P, B_MR><<<nb, BLAS_B, 0, st>>>(bp); break;
         default: throw Error(BPP_ERR_INVALID_ARG, "bad blas op");
     }
     count_launch();

@@ -50,7 +50,8 @@ enum BlasOp {
     B_CG_XR,           // x += alpha p; r -= alpha w; rr, done
     B_CG_BETA,         // beta = ||z||^2 / zz; zz = ||z||^2; p = z + beta p
     B_NORM2,           // bb = ||x||^2 (no update)
-    B_NORM2X2          // bb = ||x||^2 + ||r||^2 (no update)
+    B_NORM2X2,         // bb = ||x||^2 + ||r||^2 (no update)
+    B_MR               // minimal-residual step after B_OMEGA: x += omega s; s -= omega t (no reduction)
 };
 
 struct BlasVecs {

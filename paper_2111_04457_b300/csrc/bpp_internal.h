@@ -157,7 +157,7 @@ inline size_t spinor_alloc_bytes(int prec, int64_t stride) {
 }
 inline size_t link_alloc_bytes(int prec, int64_t stride) { return (size_t)stride * link_bytes(prec); }
 
-inline SpinorView make_spinor_view(int prec, void* base, int64_t stride) {
+__host__ __device__ inline SpinorView make_spinor_view(int prec, void* base, int64_t stride) {
     SpinorView v;
     v.data = base;
     v.stride = stride;

@@ -27,6 +27,7 @@
 
 #include "blas.h"
 #include "kernels.h"
+#include "lex.h"
 #include "solver.h"
 
 namespace bpp {
@@ -35,13 +36,19 @@ int work_read(int prec, int64_t* n, double* bytes, int reset);
 
 namespace {
 
-struct LexBatches {
-    Batch hop;    // half views, real geometry, plane stride 2 * stride
-    Batch vec;    // whole fields: 2 * stride sites
-    size_t half_off = 0;   // byte offset of the odd half inside a field
+struct LexVec {
+    DevBuf buf;
+    char* p() const { return buf.as<char>(); }
 };
 
-void make_batches(LexBatches& lb, const Gauge& G, int prec, double kappa, bool clover, int nrhs, cudaStream_t st) {
+void alloc_zero(LexVec& v, size_t bytes, cudaStream_t st) {
+    v.buf.alloc(bytes, st);
+    BPP_CUDA(cudaMemsetAsync(v.buf.p, 0, bytes, st));
+}
+
+}  // namespace
+
+void lex_batches(LexBatches& lb, const Gauge& G, int prec, double kappa, bool clover, int nrhs, cudaStream_t st) {
     lb.hop.prec = lb.vec.prec = prec;
     const int64_t S2 = 2 * G.stride;
     const size_t fbytes = spinor_alloc_bytes(prec, S2);
@@ -70,21 +77,8 @@ void make_batches(LexBatches& lb, const Gauge& G, int prec, double kappa, bool c
     lb.half_off = (size_t)G.stride * 16;   // 16-byte plane entries (double2 / float4)
 }
 
-struct LexVec {
-    DevBuf buf;
-    char* p() const { return buf.as<char>(); }
-};
-
-void alloc_zero(LexVec& v, size_t bytes, cudaStream_t st) {
-    v.buf.alloc(bytes, st);
-    BPP_CUDA(cudaMemsetAsync(v.buf.p, 0, bytes, st));
-}
-
-}  // namespace
-
-// out = D in (dag = 0) or D^dag in (dag = 1) on full fields, every system.
-static void lex_apply(const LexBatches& lb, bool clover, int dag, char* in, char* out, cudaStream_t st,
-                      const int* done = nullptr, int ds = 0) {
+void lex_apply(const LexBatches& lb, bool clover, int dag, char* in, char* out, cudaStream_t st, const int* done,
+               int ds) {
     const int mode = clover ? HOP_CLOV_XPAY : HOP_XPAY;
     char* in_o = in + lb.half_off;
     char* out_o = out + lb.half_off;
@@ -118,8 +112,8 @@ int solve_lex(const Gauge& G, double kappa, bool clover, const std::vector<const
     const int dag = mode == BPP_LEX_DDAG ? 1 : 0;
 
     LexBatches L64, LP;
-    make_batches(L64, G, P64, kappa, clover, n, st);
-    make_batches(LP, G, prec, kappa, clover, n, st);
+    lex_batches(L64, G, P64, kappa, clover, n, st);
+    lex_batches(LP, G, prec, kappa, clover, n, st);
     const size_t b64 = L64.vec.vec_bytes, bP = LP.vec.vec_bytes;
     LexVec B, X, R, T64;
     for (LexVec* v : {&B, &X, &R, &T64}) alloc_zero(*v, b64, st);
