@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
                     help="solve: the timed mixed-precision solve (default); dslash: the hopping kernel alone")
     ap.add_argument("--workload", default="wilson32",
-                    choices=["wilson32", "configs0_8x8x8x8", "prop24", "uneven6", "clover48", "grad16"],
+                    choices=["wilson32", "configs0_8x8x8x8", "errors8", "prop24", "uneven6", "clover48", "grad16"],
                     help="wilson32: the default timed solve; configs0_8x8x8x8: plain FP64 dslash + solve on 8^4; prop24: 12 point sources on 24^3x48 in one "
                          "batched solve; uneven6: six lattices of uneven size in one batched solve; "
                          "clover48: Wilson-clover 48^3x96, 4 RHS, FP16 inner, with grad_b; "
@@ -638,9 +638,16 @@ def workload_results(name, dev, steps, warm):
         by = work_bytes() / (steps + warm)
         xs = torch.empty_like(b[0])
         ms1, _ = _timed(lambda: [bpp.solve(g, b[i], KAPPA, 0.0, TOL, o, x=xs) for i in range(12)], 1, 1, stream)
+        # algorithmic bytes per site and right-hand side of the batched FP32
+        # hop (links counted once per launch for the 12 sources)
+        bpp.work_read(1, reset=True)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, o, x=x)
+        n32, by32 = bpp.work_read(1, reset=True)
+        Vh = L[0] * L[1] * L[2] * L[3] // 2
         out = {"workload": "12 spin-colour point sources on 24^3x48, one batched solve (FP32 inner, FP64 outer) "
                            "to true resid 1e-10",
                "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "ms_per_rhs": ms / 12,
+               "fp32_hop_bytes_per_site_rhs": by32 / max(n32, 1) / (Vh * 12),
                "ms_12_sequential_single_rhs": ms1, "batching_speedup": ms1 / ms,
                "true_resid_max": max(s["true_resid"] for s in st)}
     elif name == "uneven6":
@@ -717,12 +724,42 @@ def workload_results(name, dev, steps, warm):
                            "link-gradient kernel",
                "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "grad_U_rel_err_vs_oracle": err,
                "oracle_s": cpu_s, "oracle_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+    elif name == "errors8":
+        # each result's error against the FP64 oracle, per precision, on 8^4
+        # (the oracle computes every site): the hopping term of Eq. (1) and
+        # the solution x of the mixed-precision solves (true residual 1e-10)
+        import oracle
+        L = (8, 8, 8, 8)
+        U_np = synth.random_links(L, seed=1)
+        g = bpp.Gauge(torch.from_numpy(U_np).to(dev), L)
+        psi = synth.gaussian_spinor(L, seed=2)
+        Vh = 2048
+        half = psi[oracle.parity_sites(L, 1)]
+        ref = oracle.hop_eo(U_np, half, KAPPA, L, 0)
+
+        def rel(a, b):
+            return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+        errs = {}
+        for nm, pr in (("f64", bpp.F64), ("f64df", bpp.F64DF), ("f32", bpp.F32), ("f16", bpp.F16)):
+            dt = torch.complex128 if pr in (bpp.F64, bpp.F64DF) else torch.complex64
+            o_ = bpp.dslash(g, torch.from_numpy(half).to(device=dev, dtype=dt), KAPPA, bpp.EVEN, pr)
+            errs["dslash_" + nm] = rel(o_.cpu().numpy().astype(np.complex128), ref)
+        x_ref = oracle.solve(U_np, psi, KAPPA, L, tol=1e-13)
+        for nm, pr in (("f64", bpp.F64), ("f32", bpp.F32), ("f16", bpp.F16)):
+            x_, st_ = bpp.solve(g, torch.from_numpy(psi).to(dev), KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=pr))
+            xn = x_.cpu().numpy()
+            errs["solve_x_" + nm + "_inner"] = rel(xn, x_ref)
+            errs["solve_true_resid_" + nm + "_inner"] = oracle.true_residual(U_np, psi, xn, KAPPA, L)
+        out = {"workload": "errors against the FP64 oracle on 8^4 (seed-1 links, kappa 0.12): the even-odd "
+                           "hopping term per precision (norm-relative, inputs in the precision's canonical type), "
+                           "and the solution x of solves to true residual 1e-10 per inner precision",
+               "ms_per_step": 0.0, "gbs": 0.0, **errs}
     torch.cuda.synchronize()
     out["steps"], out["warmup"] = steps, warm
     return out
 
 
-WORKLOADS = ["configs0_8x8x8x8", "prop24", "uneven6", "grad16", "clover48"]
+WORKLOADS = ["configs0_8x8x8x8", "errors8", "prop24", "uneven6", "grad16", "clover48"]
 
 
 def run_workload(args, rank, world):

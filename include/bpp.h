@@ -96,6 +96,11 @@ int bpp_last_error(char* buf, size_t n);
 /* Gauge field U_mu(x) of Eq. (1) (Sec. 2: "link variable U_mu(x) in SU(3)").
  * U_lex: complex128 [4][V][3][3] in device or host memory (detected); copied,
  * the caller keeps ownership.  Synchronises `stream` before returning.
+ * When every link is SU(3) to 1e-10 (|U U^dag - 1| and |row3 -
+ * conj(row1 x row2)|), the FP32 hopping kernels read only rows 1 and 2 and
+ * rebuild row 3 (48 instead of 72 bytes per link); the environment variable
+ * BPP_LINK_COMPRESSION=0, read when a solve plan or an operator call is set
+ * up, keeps the 18-real links.
  * Errors: INVALID_ARG (NULL pointer, odd L[mu], L[mu] < 2, bc not +-1),
  * OOM, CUDA. */
 int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream stream, bpp_gauge* out);
@@ -302,7 +307,9 @@ int bpp_force(bpp_gauge U, const void* x, const void* lam, double kappa, double 
  * the hopping kernel on every slab with the face terms from those buffers.
  * The face values carry exactly the arithmetic of the undecomposed kernel, so
  * the decomposed hopping term and Schur operator equal bpp_dslash and
- * bpp_schur_apply bit for bit.  Wilson fermions (no clover term). */
+ * bpp_schur_apply bit for bit when those read the 18-real links (always in
+ * FP64 and FP16; in FP32 with BPP_LINK_COMPRESSION=0, see bpp_gauge_create).
+ * Wilson fermions (no clover term). */
 typedef struct bpp_dd_s* bpp_dd;
 
 /* Combines per-slab sums: in holds nparts blocks of n doubles (slab order),

@@ -75,6 +75,7 @@ static void check_clover(const Gauge& G, double kappa, double csw) {
 
 static void build_batch(Batch& b, const Gauge& G, int prec, double kappa, bool clover, int nrhs, cudaStream_t st) {
     b.prec = prec;
+    b.comp = link_compression(G, prec);
     for (int r = 0; r < nrhs; ++r) batch_add(b, G, kappa, clover);
     b.upload(st);
 }
@@ -131,7 +132,10 @@ int bpp_gauge_create(const bpp_lattice* lat, const void* U_lex, bpp_stream strea
             }
             BPP_CUDA(cudaStreamSynchronize(st));
         } catch (...) {
-            for (int p = 0; p < NPREC; ++p) if (G->links[p]) cudaFree(G->links[p]);
+            for (int p = 0; p < NPREC; ++p) {
+                if (G->links[p]) cudaFree(G->links[p]);
+                if (G->links12[p]) cudaFree(G->links12[p]);
+            }
             delete G;
             throw;
         }
@@ -147,6 +151,7 @@ int bpp_gauge_destroy(bpp_gauge g) {
         cudaDeviceSynchronize();
         for (int p = 0; p < NPREC; ++p) {
             if (g->links[p]) cudaFree(g->links[p]);
+            if (g->links12[p]) cudaFree(g->links12[p]);
             if (g->clover[p]) cudaFree(g->clover[p]);
         }
         delete g;

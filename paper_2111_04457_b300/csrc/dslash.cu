@@ -118,6 +118,41 @@ __device__ __forceinline__ void decode(const Raw<P16>& r, cx<float> psi[12], cx<
     u[8] = mkc(a.x * r.sc, a.y * r.sc);
 }
 
+// Two-row FP32 links (the 12 reals of rows 1 and 2 in 3 planes of float4;
+// SU(3) gives row 3 as conj(row1 x row2)).
+struct Raw32c { float4 s[6]; float4 u[3]; };
+
+__device__ __forceinline__ void load_raw(Raw32c& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
+    const float4* p = static_cast<const float4*>(in.data);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r.s[k] = __ldg(p + k * in.stride + j);
+    const float4* q = static_cast<const float4*>(U.data);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.u[k] = __ldcs(q + k * U.stride + ju);
+}
+// row 3 of an SU(3) matrix from rows 1 and 2
+__device__ __forceinline__ void third_row(cx<float> u[9]) {
+    const cx<float> a = u[1] * u[5] - u[2] * u[4], b = u[2] * u[3] - u[0] * u[5], c = u[0] * u[4] - u[1] * u[3];
+    u[6] = mkc(a.r, -a.i);
+    u[7] = mkc(b.r, -b.i);
+    u[8] = mkc(c.r, -c.i);
+}
+__device__ __forceinline__ void decode(const Raw32c& r, cx<float> psi[12], cx<float> u[9]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        psi[2 * k] = mkc(r.s[k].x, r.s[k].y);
+        psi[2 * k + 1] = mkc(r.s[k].z, r.s[k].w);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        u[2 * k] = mkc(r.u[k].x, r.u[k].y);
+        u[2 * k + 1] = mkc(r.u[k].z, r.u[k].w);
+    }
+    third_row(u);
+}
+template <int P, bool C> struct RawSel { using type = Raw<P>; };
+template <> struct RawSel<P32, true> { using type = Raw32c; };
+
 // One hop term: decode, project with (1 + S gamma_MU), colour-multiply
 // (U or U^dag), reconstruct into acc.
 template <int MU, int S, bool BACK, class real>
@@ -174,9 +209,8 @@ __device__ __forceinline__ void link_mul(const cx<df64> U[9], const cx<df64> h[6
         }
 }
 
-template <int P, int MU, int S, bool BACK>
-__device__ __forceinline__ void hop_term(cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
-    using real = typename PT<P>::real;
+template <int MU, int S, bool BACK, class RAW, class real>
+__device__ __forceinline__ void hop_term(cx<real> acc[12], const RAW& raw, bool flip) {
     cx<real> psi[12], u[9];
     decode(raw, psi, u);
     hop_term_dec<MU, S, BACK>(acc, psi, u, flip);
@@ -199,17 +233,17 @@ __device__ __forceinline__ void hop_term_dec_d(int d, cx<real> acc[12], const cx
 }
 
 // Direction d = 2 mu + (0 forward, 1 backward); SF is the forward projector sign.
-template <int P, int SF>
-__device__ __forceinline__ void hop_term_d(int d, cx<typename PT<P>::real> acc[12], const Raw<P>& raw, bool flip) {
+template <int SF, class RAW, class real>
+__device__ __forceinline__ void hop_term_d(int d, cx<real> acc[12], const RAW& raw, bool flip) {
     switch (d) {
-        case 0: hop_term<P, 0, SF, false>(acc, raw, flip); break;
-        case 1: hop_term<P, 0, -SF, true>(acc, raw, flip); break;
-        case 2: hop_term<P, 1, SF, false>(acc, raw, flip); break;
-        case 3: hop_term<P, 1, -SF, true>(acc, raw, flip); break;
-        case 4: hop_term<P, 2, SF, false>(acc, raw, flip); break;
-        case 5: hop_term<P, 2, -SF, true>(acc, raw, flip); break;
-        case 6: hop_term<P, 3, SF, false>(acc, raw, flip); break;
-        default: hop_term<P, 3, -SF, true>(acc, raw, flip); break;
+        case 0: hop_term<0, SF, false>(acc, raw, flip); break;
+        case 1: hop_term<0, -SF, true>(acc, raw, flip); break;
+        case 2: hop_term<1, SF, false>(acc, raw, flip); break;
+        case 3: hop_term<1, -SF, true>(acc, raw, flip); break;
+        case 4: hop_term<2, SF, false>(acc, raw, flip); break;
+        case 5: hop_term<2, -SF, true>(acc, raw, flip); break;
+        case 6: hop_term<3, SF, false>(acc, raw, flip); break;
+        default: hop_term<3, -SF, true>(acc, raw, flip); break;
     }
 }
 
@@ -315,7 +349,7 @@ __device__ __forceinline__ void hop_halo_bwd(cx<typename PT<P>::real> acc[12], c
     reconstruct<3, SB>(acc, g);
 }
 
-template <int P, bool DAG, int MODE, bool DD = false>
+template <int P, bool DAG, int MODE, bool DD = false, bool C = false>
 __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::value) k_hop(HopParams hp) {
     using real = typename PT<P>::real;
     int s, tile;
@@ -351,14 +385,14 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     const bool top = DD && x4 == g.L[3] - 1, bot = DD && x4 == 0;
     const int64_t fidx = DD ? (int64_t)i - (int64_t)g.Lh * g.L[1] * g.L[2] * x4 : 0;
     if (HopPrefetch<P>::value) {
-        Raw<P> cur, nxt;
+        typename RawSel<P, C>::type cur, nxt;
         load_raw(cur, in, jn[0], d.U[p][0], ju[0]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if (k < 7) load_raw(nxt, in, jn[k + 1], d.U[((k + 1) & 1) ? q : p][(k + 1) >> 1], ju[k + 1]);
             if (DD && k == 6 && top) hop_halo_fwd<P, SF>(acc, hp, s, fidx, d.U[p][3], i, hp.flip_top != 0);
             else if (DD && k == 7 && bot) hop_halo_bwd<P, -SF>(acc, hp, s, fidx, hp.flip_bot != 0);
-            else hop_term_d<P, SF>(k, acc, cur, flip[k]);
+            else hop_term_d<SF>(k, acc, cur, flip[k]);
             if (k < 7) cur = nxt;
         }
     } else {
@@ -369,9 +403,9 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
             } else if (DD && k == 7 && bot) {
                 hop_halo_bwd<P, -SF>(acc, hp, s, fidx, hp.flip_bot != 0);
             } else {
-                Raw<P> cur;
+                typename RawSel<P, C>::type cur;
                 load_raw(cur, in, jn[k], d.U[(k & 1) ? q : p][k >> 1], ju[k]);
-                hop_term_d<P, SF>(k, acc, cur, flip[k]);
+                hop_term_d<SF>(k, acc, cur, flip[k]);
             }
         }
     }
@@ -513,6 +547,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     hp.y = y;
     hp.a_sign = a_sign;
     const std::string key = "hop" + std::to_string(P) + (DAG ? "d" : "n") + std::to_string(MODE) + (dd ? "dd" : "") +
+                            (b.comp ? "c" : "") +
                             "_" + std::to_string(b.Vh_max) + "x" + std::to_string(b.nsys()) + (b.uniform ? "u" : "r");
     const bool may_tune = out != y && out != in;
     auto run = [&](int B) {
@@ -524,10 +559,16 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
                 return;
             }
         }
+        if constexpr (P == P32) {
+            if (b.comp) {
+                k_hop<P, DAG, MODE, false, true><<<nb, B, 0, st>>>(hp);
+                return;
+            }
+        }
         k_hop<P, DAG, MODE><<<nb, B, 0, st>>>(hp);
     };
     // right-hand sides of one gauge field can share each link load in registers
-    bool shared = !dd && b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
+    bool shared = !dd && !b.comp && b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
     for (int s = 1; shared && s < b.nsys(); ++s) shared = b.sys[s].U[0][0].data == b.sys[0].U[0][0].data;
     auto run_multi = [&](int R, int B) {
         BlockMap m;
@@ -578,7 +619,8 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     // algorithmic bytes: systems that share a gauge field (the right-hand sides
     // of one lattice) read its links once per launch
     double sites = 0, bytes = 0;
-    const double bps = hop_bytes_per_site(P, MODE), lbytes = 8.0 * link_bytes(P);
+    const double lb = b.comp ? 48.0 : (double)link_bytes(P);
+    const double bps = hop_bytes_per_site(P, MODE) - 8.0 * (link_bytes(P) - lb), lbytes = 8.0 * lb;
     std::vector<double> per_sys(b.nsys());
     for (int s = 0; s < b.nsys(); ++s) {
         bool first = true;

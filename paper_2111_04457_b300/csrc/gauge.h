@@ -10,6 +10,10 @@ struct bpp_gauge_s {
     int64_t V = 0, Vh = 0, stride = 0;
     int device = 0;
     void* links[bpp::NPREC] = {};    // per storage format: 8 link fields [parity][mu]
+    // every link is SU(3) (checked at creation): FP32 also keeps the two-row
+    // form (rows 1 and 2; row 3 = conj(row1 x row2) is rebuilt)
+    bool su3 = false;
+    void* links12[bpp::NPREC] = {};  // FP32: 3 planes of float4
     bool has_clover = false;
     double clov_kappa = 0.0, clov_csw = 0.0;
     void* clover[bpp::NPREC] = {};   // per storage format: A_e, A_o, Ainv_e, Ainv_o
@@ -21,6 +25,15 @@ using Gauge = bpp_gauge_s;
 
 inline size_t clover_alloc_bytes(int prec, int64_t stride) {
     return (size_t)stride * ((prec == P64 || prec == P64S) ? 576 : prec == P32 ? 288 : 144);
+}
+
+inline size_t link12_alloc_bytes(int prec, int64_t stride) { return (size_t)stride * (prec == P32 ? 48 : 0); }
+
+inline LinkView link12_view(const Gauge& G, int prec, int parity, int mu) {
+    LinkView v;
+    v.data = static_cast<const char*>(G.links12[prec]) + (size_t)(parity * 4 + mu) * link12_alloc_bytes(prec, G.stride);
+    v.stride = G.stride;
+    return v;
 }
 
 inline LinkView link_view(const Gauge& G, int prec, int parity, int mu) {
@@ -48,6 +61,9 @@ struct Batch {
     size_t vec_bytes = 0;   // bytes of one batch vector (all systems, one parity)
     bool uniform = true;
     int Vh_max = 0;
+    // FP32: the systems' links in the two-row form (set before the first
+    // batch_add; every gauge added must then be SU(3))
+    bool comp = false;
     void upload(cudaStream_t s) {
         dsys.alloc(sys.size() * sizeof(SysDesc), s);
         BPP_CUDA(cudaMemcpyAsync(dsys.p, sys.data(), sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
@@ -64,6 +80,9 @@ struct Batch {
 
 // Appends one system on gauge G (kappa, clover if csw != 0) to batch b.
 void batch_add(Batch& b, const Gauge& G, double kappa, bool clover);
+// Whether hopping kernels on gauge G in precision prec may use the two-row
+// links (G is SU(3), prec is FP32, and BPP_LINK_COMPRESSION is not 0).
+bool link_compression(const Gauge& G, int prec);
 // Grid and block map for a launch over all systems with `sites_per_block`.
 BlockMap block_map(const Batch& b, int sites_per_block, int& nblocks);
 

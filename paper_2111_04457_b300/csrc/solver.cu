@@ -148,6 +148,12 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     pl->b64s.prec = P64S;
     pl->b32.prec = P32;
     pl->reliable = split && prec == P16;
+    // two-row links for the reduced-precision hops when every gauge is SU(3)
+    pl->bP.comp = pl->b32.comp = true;
+    for (auto* g : G) {
+        pl->bP.comp = pl->bP.comp && link_compression(*g, prec);
+        pl->b32.comp = pl->b32.comp && link_compression(*g, P32);
+    }
     for (size_t s = 0; s < G.size(); ++s) {
         batch_add(pl->b64, *G[s], kappa[s], clover);
         batch_add(pl->bP, *G[s], kappa[s], clover);

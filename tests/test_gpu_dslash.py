@@ -135,3 +135,32 @@ def test_dslash_multi_rhs_low_precision(prec, nrhs):
             assert rel_err(out[r], one) <= (1e-6 if prec == 1 else 5e-3)
         ref = oracle.hop_eo(round32(U) if prec == 1 else U, psis[nrhs - 1], KAPPA, L, parity, BC)
         assert rel_err(out[nrhs - 1], ref) <= (1e-6 if prec == 1 else 5e-3)
+
+
+@pytest.mark.parametrize("L", [(6, 6, 6, 10), (2, 4, 2, 6)])
+def test_dslash_two_row_links(L, monkeypatch):
+    """Exact SU(3) links: the FP32 hop reads the two-row form (row 3 rebuilt
+    as conj(row1 x row2); 48 B per link in the work counter), agrees with the
+    oracle on the FP64 links to 1e-6 and with the 18-real form; links that are
+    not SU(3) to 1e-10 keep the 18-real form, and FP16 always does."""
+    bpp = lib()
+    prec, tol, spin, full = 1, 1e-6, 96, 72
+    g, U = gauge(L)
+    Vh = oracle.volume(L) // 2
+    psi = synth.gaussian_spinor(L, seed=2)[:Vh]
+    ref = oracle.hop_eo(U, psi, KAPPA, L, 0, BC)
+    bpp.work_read(prec, reset=True)
+    out = to_np(bpp.dslash(g, to_dev(psi, torch.complex64), KAPPA, 0, prec))
+    assert bpp.work_read(prec, reset=True)[1] == Vh * (8 * 48 + 2 * spin)
+    assert rel_err(out, ref) <= tol
+    monkeypatch.setenv("BPP_LINK_COMPRESSION", "0")
+    out18 = to_np(bpp.dslash(g, to_dev(psi, torch.complex64), KAPPA, 0, prec))
+    assert bpp.work_read(prec, reset=True)[1] == Vh * (8 * full + 2 * spin)
+    assert rel_err(out, out18) <= tol
+    monkeypatch.delenv("BPP_LINK_COMPRESSION")
+    g32, _ = gauge(L, round32(U))          # FP32-rounded: unitary only to ~1e-7
+    bpp.dslash(g32, to_dev(psi, torch.complex64), KAPPA, 0, prec)
+    assert bpp.work_read(prec, reset=True)[1] == Vh * (8 * full + 2 * spin)
+    bpp.work_read(2, reset=True)
+    bpp.dslash(g, to_dev(psi, torch.complex64), KAPPA, 0, 2)
+    assert bpp.work_read(2, reset=True)[1] == Vh * (8 * 36 + 2 * 52)
