@@ -50,10 +50,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--inner-tol", type=float, default=None, help="inner relative tolerance")
     ap.add_argument("--eager", action="store_true", help="host-driven inner loop instead of CUDA graphs")
+    ap.add_argument("--outer-arith", type=int, default=2, choices=[0, 1, 2],
+                    help="outer loop: 0 FP64; 1 double-float defects, FP64 true-residual check; "
+                         "2 double-float defects and check (x returned as the checked iterate's FP64 value)")
     ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
                     help="solve: the timed mixed-precision solve (default); dslash: the hopping kernel alone")
     ap.add_argument("--workload", default="wilson32",
-                    choices=["wilson32", "configs0_8x8x8x8", "errors8", "prop24", "uneven6", "clover48", "grad16"],
+                    choices=["wilson32", "configs0_8x8x8x8", "errors8", "prop24", "uneven6", "clover48", "grad16",
+                             "mg16", "dd16"],
                     help="wilson32: the default timed solve; configs0_8x8x8x8: plain FP64 dslash + solve on 8^4; prop24: 12 point sources on 24^3x48 in one "
                          "batched solve; uneven6: six lattices of uneven size in one batched solve; "
                          "clover48: Wilson-clover 48^3x96, 4 RHS, FP16 inner, with grad_b; "
@@ -195,11 +199,17 @@ def cpu_oracle_sample(L, target_s=12.0):
     return total_sites * BYTES_F64 / total_t / 1e9, total_sites, total_t, threads
 
 
-def solve_config(L, inner_name, world=1):
+OUTER_NAMES = {0: "FP64 defect correction", 1: "defect correction with double-float defects and an FP64 "
+                                              "true-residual check",
+               2: "defect correction in double-float arithmetic (defects and true-residual check; x returned "
+                  "in FP64 and re-checked with the FP64 D)"}
+
+
+def solve_config(L, inner_name, world=1, outer_arith=2):
     """The benchmark workload as reported in `config` (shared by both arms)."""
     return {"workload": f"Wilson eo-BiCGStab solve, {'x'.join(map(str, L))}, kappa {KAPPA}, 1 Gaussian RHS, "
-                        f"{inner_name} inner + FP64 defect correction to true resid {TOL}",
-            "lattice": list(L), "kappa": KAPPA, "tol": TOL, "rhs": 1,
+                        f"{inner_name} inner + {OUTER_NAMES[outer_arith]} to true resid {TOL}",
+            "lattice": list(L), "kappa": KAPPA, "tol": TOL, "rhs": 1, "outer_arith": outer_arith,
             "l2": "inputs larger than L2 (links 1.2 GB FP64 / 0.6 GB FP32 / 0.3 GB FP16); no flush",
             "parallelism": f"replicas x{world}"}
 
@@ -220,7 +230,7 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": solve_config(L, "f16-storage/f32" if args.inner == "f16" else "f32"),
+           "config": solve_config(L, "f16-storage/f32" if args.inner == "f16" else "f32", 1, args.outer_arith),
            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
                             "sample": "the oracle's FP64 D (Eq. 1, plain C loops, OpenMP) on random site samples of "
                                       "this lattice, ~4 s per step, as the even-odd dslash work of the solve: "
@@ -250,7 +260,8 @@ def run_ours(args, rank, world):
     del U
     b = torch.from_numpy(b_np).to(dev)
     x = torch.empty_like(b)
-    opts = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0 if args.eager else 2)
+    opts = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0 if args.eager else 2,
+                          outer_arith=args.outer_arith)
     stream = torch.cuda.current_stream()
 
     # warm-up (also runs the block-size autotuner on first use)
@@ -285,6 +296,10 @@ def run_ours(args, rank, world):
     hop_bytes_all = allreduce_sum(hop_bytes, world, dev)
     value = hop_bytes_all / (ms / 1000.0) / 1e9
     true_res = max(s["true_resid"] for s in stats)
+    # the returned x re-checked with the FP64 D of Eq. (1) (a separate kernel
+    # path from the solver's own check)
+    true_res_fp64 = (torch.linalg.vector_norm(b - bpp.dirac_apply(g, x, KAPPA)) /
+                     torch.linalg.vector_norm(b)).item()
 
     # per-class timing of one more solve of the same workload, host-driven (no
     # graphs, convergence checked every 4 inner iterations, so a few more
@@ -293,7 +308,8 @@ def run_ours(args, rank, world):
     bpp.prof_enable(True)
     for c in CLASS_NAMES:
         bpp.prof_read(c, reset=True)
-    bpp.solve(g, b, KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0), x=x)
+    bpp.solve(g, b, KAPPA, 0.0, TOL, bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0,
+                                                    outer_arith=args.outer_arith), x=x)
     torch.cuda.synchronize()
     bpp.prof_enable(False)
     prof = {c: bpp.prof_read(c, reset=False) for c in (0, 1, 2, 3)}
@@ -387,6 +403,19 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         native_outer_ms = e0.elapsed_time(e1)
+    # the same solve with the true-residual check in FP64 arithmetic
+    fp64_check_ms = None
+    if args.outer_arith == 2:
+        oc = bpp.solve_opts(inner_prec=inner, inner_tol=args.inner_tol, use_graph=0 if args.eager else 2,
+                            outer_arith=1)
+        for _ in range(3):
+            bpp.solve(g, b, KAPPA, 0.0, TOL, oc, x=x)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bpp.solve(g, b, KAPPA, 0.0, TOL, oc, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_check_ms = e0.elapsed_time(e1)
     f32_ms = None
     if inner != bpp.F32:
         o32 = bpp.solve_opts(inner_prec=bpp.F32)
@@ -413,7 +442,7 @@ def run_ours(args, rank, world):
         bpp.release_workspace()
         for name in WORKLOADS:
             steps = 2 if name == "clover48" else 5
-            workloads[name] = workload_results(name, dev, steps, 1)
+            workloads[name] = workload_results(name, dev, steps, 3)
             torch.cuda.synchronize()
             bpp.release_workspace()
 
@@ -425,14 +454,18 @@ def run_ours(args, rank, world):
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": f"{inner_name} inner, f64 outer", "data": "synthetic",
-        "config": solve_config(L, inner_name, world),
+        "vs_baseline": None,
+        "dtype": f"{inner_name} inner, {'double-float' if args.outer_arith == 2 else 'f64'} outer", "data": "synthetic",
+        "config": solve_config(L, inner_name, world, args.outer_arith),
         "solve_ms": ms_step,
         "solve_ms_fp64": fp64_ms,
         "solve_ms_f32_inner": f32_ms,
         "solve_ms_fp64_outer_defects": native_outer_ms,
         "speedup_vs_fp64": (fp64_ms / ms_step) if fp64_ms else None,
         "true_resid": true_res,
+        "true_resid_fp64_recheck": true_res_fp64,
+        "outer_arith": args.outer_arith,
+        "solve_ms_fp64_check": fp64_check_ms,
         "inner_tol": inner_tol,
         "graphs": not args.eager,
         "inner_iters": stats[-1]["inner_iters"], "outer_iters": stats[-1]["outer_iters"],
@@ -637,7 +670,7 @@ def workload_results(name, dev, steps, warm):
         ms, st = _timed(lambda: bpp.solve(g, b, KAPPA, 0.0, TOL, o, x=x)[1], steps, warm, stream)
         by = work_bytes() / (steps + warm)
         xs = torch.empty_like(b[0])
-        ms1, _ = _timed(lambda: [bpp.solve(g, b[i], KAPPA, 0.0, TOL, o, x=xs) for i in range(12)], 1, 1, stream)
+        ms1, _ = _timed(lambda: [bpp.solve(g, b[i], KAPPA, 0.0, TOL, o, x=xs) for i in range(12)], 1, warm, stream)
         # algorithmic bytes per site and right-hand side of the batched FP32
         # hop (links counted once per launch for the 12 sources)
         bpp.work_read(1, reset=True)
@@ -660,7 +693,7 @@ def workload_results(name, dev, steps, warm):
         work_bytes()
         ms, st = _timed(lambda: bpp.solve_batch(gs, bs, kap, TOL, o, xs=xs)[1], steps, warm, stream)
         by = work_bytes() / (steps + warm)
-        ms1, _ = _timed(lambda: [bpp.solve(gs[i], bs[i], kap[i], 0.0, TOL, o, x=xs[i]) for i in range(6)], 1, 1,
+        ms1, _ = _timed(lambda: [bpp.solve(gs[i], bs[i], kap[i], 0.0, TOL, o, x=xs[i]) for i in range(6)], 1, warm,
                         stream)
         out = {"workload": "6 lattices 8^4 12^4 16^4 16^3x32 20^3x40 24^3x48 (1204992 sites), kappa U[0.10,0.12], "
                            "one batched solve (FP32 inner, FP64 outer) to true resid 1e-10",
@@ -724,6 +757,49 @@ def workload_results(name, dev, steps, warm):
                            "link-gradient kernel",
                "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "grad_U_rel_err_vs_oracle": err,
                "oracle_s": cpu_s, "oracle_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+    elif name == "mg16":
+        # multigrid-preconditioned GCR (FP32, FP64 defect correction) against
+        # the lexical BiCGStab with the same outer loop, 16^3x32, kappa 0.12
+        L = (16, 16, 16, 32)
+        g = bpp.Gauge(torch.from_numpy(synth.random_links(L, seed=1)).to(dev), L)
+        b = torch.from_numpy(synth.gaussian_spinor(L, seed=2)).to(dev)
+        vecs = torch.from_numpy(np.stack([synth.gaussian_spinor(L, seed=60 + k) for k in range(6)])).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mg = bpp.Multigrid(g, KAPPA, vecs, (4, 4, 4, 4), refine=1)
+        torch.cuda.synchronize()
+        setup_ms = 1000 * (time.perf_counter() - t0)
+        o = bpp.solve_opts(max_inner=200)
+        ms, st = _timed(lambda: mg.solve(b, TOL, o)[1], steps, warm, stream)
+        ol = bpp.solve_opts(inner_prec=bpp.F32)
+        ms_l, st_l = _timed(lambda: bpp.solve_lex(g, b, KAPPA, 0.0, TOL, bpp.LEX_D, ol)[1], steps, warm, stream)
+        out = {"workload": "16^3x32 Wilson, kappa 0.12, one Gaussian RHS: two-level multigrid (4^4 blocks, 6 "
+                           "near-null vectors from one inverse-iteration pass) preconditioning flexible GCR in FP32 "
+                           "under FP64 defect correction, against lexical BiCGStab (FP32 inner, same outer loop)",
+               "ms_per_step": ms, "gbs": 0.0, "setup_ms": setup_ms, "gcr_iters": st[0]["inner_iters"],
+               "true_resid": st[0]["true_resid"], "lex_bicgstab_ms": ms_l,
+               "lex_bicgstab_iters": st_l[0]["inner_iters"], "lex_true_resid": st_l[0]["true_resid"]}
+        del mg
+    elif name == "dd16":
+        # the decomposed FP64 solve (slabs in x4 on this GPU) against the
+        # undecomposed FP64 solve, 16^3x32
+        L = (16, 16, 16, 32)
+        U = torch.from_numpy(synth.random_links(L, seed=1)).to(dev)
+        g = bpp.Gauge(U, L)
+        b = torch.from_numpy(synth.gaussian_spinor(L, seed=2)).to(dev)
+        o = bpp.solve_opts(inner_prec=bpp.F64, use_graph=0)
+        ms0, st0 = _timed(lambda: bpp.solve(g, b, KAPPA, 0.0, TOL, o)[1], steps, warm, stream)
+        out = {"workload": "16^3x32 Wilson FP64 even-odd BiCGStab to 1e-10: decomposition into 2 and 4 slabs in x4 "
+                           "(faces exchanged by device copies, per-slab reductions summed across slabs) against the "
+                           "undecomposed host-driven solve",
+               "ms_per_step": ms0, "gbs": 0.0, "undecomposed_ms": ms0, "undecomposed_iters": st0[0]["inner_iters"]}
+        for nd in (2, 4):
+            dd = bpp.DomainDecomposition(U, L, nd)
+            msd, std = _timed(lambda: dd.solve(b, KAPPA, TOL)[1], steps, warm, stream)
+            out[f"slabs{nd}_ms"] = msd
+            out[f"slabs{nd}_iters"] = std[0]["inner_iters"]
+            out[f"slabs{nd}_true_resid"] = std[0]["true_resid"]
+            del dd
     elif name == "errors8":
         # each result's error against the FP64 oracle, per precision, on 8^4
         # (the oracle computes every site): the hopping term of Eq. (1) and
@@ -759,7 +835,7 @@ def workload_results(name, dev, steps, warm):
     return out
 
 
-WORKLOADS = ["configs0_8x8x8x8", "errors8", "prop24", "uneven6", "grad16", "clover48"]
+WORKLOADS = ["configs0_8x8x8x8", "errors8", "prop24", "uneven6", "grad16", "mg16", "dd16", "clover48"]
 
 
 def run_workload(args, rank, world):
@@ -768,7 +844,7 @@ def run_workload(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    r = workload_results(args.workload, dev, args.steps, max(args.warmup, 1))
+    r = workload_results(args.workload, dev, args.steps, max(args.warmup, 3))
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": r["gbs"], "unit": "GB/s", "n_gpus": world, "steps": r["steps"],
                           "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True,

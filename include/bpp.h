@@ -204,7 +204,16 @@ typedef struct {
                          bhat - Mhat x in double-float arithmetic (FP64 values held as
                          FP32 hi + lo pairs, ~48-bit significands, on the FP32 pipe),
                          while the solution, its accumulation, all norms and the final
-                         true residual stay FP64; ignored (FP64) when inner_prec is F64 */
+                         true residual stay FP64;
+                         2: as 1, and the true-residual check and the iterate x in
+                         double-float too: x_o = A_oo^-1 (b_o + kappa H_oe x_e) and
+                         the even residual b_e - (A_ee x_e - kappa H_eo x_o) are
+                         computed in double-float (the odd residual vanishes by
+                         construction), and the returned x is the checked iterate's
+                         exact FP64 value.  The check's rounding error is of order
+                         1e-14 ||x|| / ||b|| relative, against the FP64 pipe's 1/64
+                         rate on this GPU.  Ignored (FP64) when inner_prec is F64;
+                         other values: INVALID_ARG */
 } bpp_solve_opts;
 
 /* Per right-hand side statistics of a solve. */
@@ -213,8 +222,11 @@ typedef struct {
     int inner_iters;    /* total inner Krylov iterations */
     int converged;      /* 1 if true_resid <= tol */
     int status;         /* BPP_OK or the per-RHS error code */
-    double true_resid;  /* ||b - D x|| / ||b||, full FP64 D recomputed from scratch */
-    double seconds;     /* wall time of the whole call (same for every RHS) */
+    double true_resid;  /* ||b - D x|| / ||b|| with the full D recomputed from x (FP64, or
+                           double-float with outer_arith 2) */
+    double seconds;     /* wall time of the whole call (same for every RHS); the first call
+                           of a configuration includes the block-size autotuner's timing
+                           launches and the CUDA-graph capture */
     double hop_bytes;   /* algorithmic bytes of every hopping-kernel launch of the call (all RHS) */
     double hop_gbs;     /* hop_bytes / seconds / 1e9: the dslash GB/s the call sustained */
 } bpp_solve_stats;
@@ -263,7 +275,10 @@ int bpp_solve_lex(bpp_gauge U, const void* b, void* x, double kappa, double csw,
 
 /* Batched solve over nlat independent lattices (each with its own gauge
  * handle, hopping parameter kappa[i] and one right-hand side), run together so
- * every kernel launch covers all lattices.  csw != 0: Wilson-clover, each
+ * every kernel launch covers all lattices.  The paper has no counterpart (its
+ * solver objects take one lattice per call); the batch is this library's
+ * extension for many small independent problems on one GPU, each system
+ * following the bpp_solve algorithm of Sec. 2 on its own.  csw != 0: Wilson-clover, each
  * gauge handle must hold its clover term built with (kappa[i], csw).
  * b[i], x[i]: device complex128 [V_i][4][3].  stats: NULL or nlat entries.
  * Errors: as bpp_solve. */

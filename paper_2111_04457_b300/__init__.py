@@ -311,12 +311,14 @@ def dirac_apply(g: Gauge, x: torch.Tensor, kappa: float, csw: float = 0.0, dagge
 
 
 def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000, max_outer=50, dagger=False,
-               check_every=4, use_x0=False, use_graph=2, outer_df64=True) -> SolveOpts:
+               check_every=4, use_x0=False, use_graph=2, outer_df64=True, outer_arith=None) -> SolveOpts:
     """Solver options (bpp_solve_opts).  use_graph: 0 host-driven, 1 inner loop as
     a CUDA graph, 2 whole correction loop as one graph launch (default).
-    outer_df64: intermediate defects of the FP64 outer loop in double-float
-    arithmetic (the final true residual, the solution accumulation and the
-    norms stay FP64)."""
+    outer_arith: 0 every outer-loop operator in FP64; 1 the preparation and the
+    intermediate defects in double-float arithmetic, the true-residual check and
+    the solution accumulation in FP64; 2 the check and the iterate in
+    double-float too (the returned x is the checked iterate's exact FP64 value).
+    None keeps the library default; outer_df64=False is outer_arith=0."""
     o = SolveOpts()
     _lib.bpp_solve_opts_default(ctypes.byref(o))
     o.solver = solver
@@ -329,7 +331,12 @@ def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000,
     o.check_every = check_every
     o.use_x0 = int(use_x0)
     o.use_graph = int(use_graph)
-    o.outer_arith = int(outer_df64)
+    if outer_arith is not None:
+        if int(outer_arith) not in (0, 1, 2):
+            raise ValueError("outer_arith must be 0, 1 or 2")
+        o.outer_arith = int(outer_arith)
+    elif not outer_df64:
+        o.outer_arith = 0
     return o
 
 

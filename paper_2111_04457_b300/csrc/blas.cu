@@ -14,6 +14,16 @@ constexpr int BLAS_B = 256;
 #endif
 constexpr int BLAS_SPT = BPP_BLAS_SPT;   // sites per thread
 
+// Threads per block of the vector kernels: 256, or fewer on small lattices so
+// that the grid still spans about two blocks per SM (on few SMs the FP64 work
+// of a small lattice is bound by the FP64 pipe, 1/64 of the FP32 rate).
+static int vec_block(const Batch& b) {
+    const int64_t S = b.sites();
+    int B = BLAS_B;
+    while (B > 32 && S < (int64_t)B * 2 * 148) B >>= 1;
+    return B;
+}
+
 void RedBuf::ensure(int nblocks, int nsys, cudaStream_t st) {
     if (nblocks > cap_blocks) {
         BPP_REQUIRE(!capturing(st), BPP_ERR_CUDA, "reduction buffer must be sized before graph capture");
@@ -226,7 +236,7 @@ __global__ void k_blas_fin(KScal* sc, const double* tot, int n) {
 
 // Each block covers BLAS_SPT * BLAS_B sites of one system, so the last block
 // of a reduction sums few per-block partials.
-template <int P, int OP>
+template <int P, int OP, int SPT>
 __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     int s, tile;
     map_block(bp.map, s, tile);
@@ -238,10 +248,10 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
     using real = typename PT<P>::real;
     real red[4] = {0, 0, 0, 0};
     if (active) {
-        const int base = tile * (BLAS_SPT * BLAS_B) + threadIdx.x;
+        const int base = tile * (SPT * blockDim.x) + threadIdx.x;
 #pragma unroll
-        for (int k = 0; k < BLAS_SPT; ++k) {
-            const int i = base + k * BLAS_B;
+        for (int k = 0; k < SPT; ++k) {
+            const int i = base + k * blockDim.x;
             if (i < d.g.Vh) blas_site<P, OP>(bp, d, i, al, om, be, red);
         }
     }
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(BLAS_B) k_blas(BlasParams bp) {
 }
 
 // p = z + beta p for CGNR (separate: needs the finalised beta)
-template <int P>
+template <int P, int SPT>
 __global__ void __launch_bounds__(BLAS_B) k_cg_p(BlasParams bp) {
     using real = typename PT<P>::real;
     int s, tile;
@@ -269,8 +279,8 @@ __global__ void __launch_bounds__(BLAS_B) k_cg_p(BlasParams bp) {
     if (bp.sc[s].done) return;
     const real be = (real)bp.sc[s].beta.x;
 #pragma unroll
-    for (int k = 0; k < BLAS_SPT; ++k) {
-        const int i = tile * (BLAS_SPT * BLAS_B) + k * BLAS_B + threadIdx.x;
+    for (int k = 0; k < SPT; ++k) {
+        const int i = tile * (SPT * blockDim.x) + k * blockDim.x + threadIdx.x;
         if (i >= d.g.Vh) break;
         cx<real> a[12], b[12];
         Access<P>::load_spinor(sys_view<P>(bp.v.z, d), i, a);
@@ -289,7 +299,11 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
     bp.red_out = red_out;
     bp.sys = bt.dev();
     int nb = 0;
-    bp.map = block_map(bt, BLAS_B * BLAS_SPT, nb);
+    // BLAS_SPT sites per thread on large batches (few partials per reduction),
+    // one per thread and smaller blocks on small ones
+    const bool big = bt.sites() >= (int64_t)2 * 148 * BLAS_B * BLAS_SPT;
+    const int vb = big ? BLAS_B : vec_block(bt);
+    bp.map = block_map(bt, vb * (big ? BLAS_SPT : 1), nb);
     rb.ensure(nb, bt.nsys(), st);
     bp.v = vv;
     bp.sc = sc;
@@ -298,27 +312,34 @@ static void blas_t(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBu
     // vectors each op reads plus writes (its algorithmic traffic per site)
     static const int passes[] = {5, 2, 3, 2, 7, 4, 3, 2, 1, 6, 4, 1, 2, 5};
     ProfScope prof(PROF_BLAS, bt.sites() * spinor_bytes(P) * passes[op], st);
+#define K_BLAS(OPC)                                                      \
+    do {                                                                  \
+        if (big) k_blas<P, OPC, BLAS_SPT><<<nb, vb, 0, st>>>(bp);         \
+        else k_blas<P, OPC, 1><<<nb, vb, 0, st>>>(bp);                    \
+    } while (0)
     switch (op) {
-        case B_INIT_BICG: k_blas<P, B_INIT_BICG><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_ALPHA: k_blas<P, B_ALPHA><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_S: k_blas<P, B_S><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_OMEGA: k_blas<P, B_OMEGA><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_XR: k_blas<P, B_XR><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_P: k_blas<P, B_P><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_CG_INIT: k_blas<P, B_CG_INIT><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_CG_PZ: k_blas<P, B_CG_PZ><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_CG_ALPHA: k_blas<P, B_CG_ALPHA><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_CG_XR: k_blas<P, B_CG_XR><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_INIT_BICG: K_BLAS(B_INIT_BICG); break;
+        case B_ALPHA: K_BLAS(B_ALPHA); break;
+        case B_S: K_BLAS(B_S); break;
+        case B_OMEGA: K_BLAS(B_OMEGA); break;
+        case B_XR: K_BLAS(B_XR); break;
+        case B_P: K_BLAS(B_P); break;
+        case B_CG_INIT: K_BLAS(B_CG_INIT); break;
+        case B_CG_PZ: K_BLAS(B_CG_PZ); break;
+        case B_CG_ALPHA: K_BLAS(B_CG_ALPHA); break;
+        case B_CG_XR: K_BLAS(B_CG_XR); break;
         case B_CG_BETA:
-            k_blas<P, B_CG_BETA><<<nb, BLAS_B, 0, st>>>(bp);
+            K_BLAS(B_CG_BETA);
             count_launch();
-            k_cg_p<P><<<nb, BLAS_B, 0, st>>>(bp);
+            if (big) k_cg_p<P, BLAS_SPT><<<nb, vb, 0, st>>>(bp);
+            else k_cg_p<P, 1><<<nb, vb, 0, st>>>(bp);
             break;
-        case B_NORM2: k_blas<P, B_NORM2><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_NORM2X2: k_blas<P, B_NORM2X2><<<nb, BLAS_B, 0, st>>>(bp); break;
-        case B_MR: k_blas<P, B_MR><<<nb, BLAS_B, 0, st>>>(bp); break;
+        case B_NORM2: K_BLAS(B_NORM2); break;
+        case B_NORM2X2: K_BLAS(B_NORM2X2); break;
+        case B_MR: K_BLAS(B_MR); break;
         default: throw Error(BPP_ERR_INVALID_ARG, "bad blas op");
     }
+#undef K_BLAS
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -434,20 +455,22 @@ __global__ void __launch_bounds__(BLAS_B, OuterAccMinBlocks<P>::value) k_outer_a
     cx<real> e[12];
     Access<P>::load_spinor(sys_view<P>(op.b, op.sP[s]), i, e);
     // component by component (no whole FP64 or split spinor held in registers)
-    double2* xp = reinterpret_cast<double2*>(op.a + d.vec_off);
+    double2* xp = op.a ? reinterpret_cast<double2*>(op.a + d.vec_off) : nullptr;
     float4* xsp = op.c ? reinterpret_cast<float4*>(op.c + d.vec_off) : nullptr;
     const df64 scd(sc);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
         const int64_t j = k * d.stride + i;
-        double2 xv = xp[j];
-        xv.x = fma(sc, (double)e[k].r, xv.x);
-        xv.y = fma(sc, (double)e[k].i, xv.y);
-        xp[j] = xv;
+        if (xp) {
+            double2 xv = xp[j];
+            xv.x = fma(sc, (double)e[k].r, xv.x);
+            xv.y = fma(sc, (double)e[k].i, xv.y);
+            xp[j] = xv;
+        }
         if (xsp) {
             // the split copy takes the same update in double-float arithmetic
-            // (no FP64 conversions); it tracks x to ~1e-14 and only feeds the
-            // defects
+            // (no FP64 conversions); beside an FP64 x it tracks x to ~1e-14 and
+            // only feeds the defects, without one (x64 null) it is the iterate
             const float4 v = xsp[j];
             const df64 r = normalized(fma(scd, to_df(e[k].r), df64(v.x, v.y)));
             const df64 m = normalized(fma(scd, to_df(e[k].i), df64(v.z, v.w)));
@@ -519,13 +542,14 @@ void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st) 
     op.s64 = b64.dev();
     op.sP = b64.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     op.a = const_cast<char*>(xs);
     op.b = x64;
     op.c = nullptr;
     op.sc = nullptr;
     ProfScope prof(PROF_OUTER, b64.sites() * 384.0, st);
-    k_split_to_f64<<<nb, BLAS_B, 0, st>>>(op);
+    k_split_to_f64<<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -553,14 +577,15 @@ void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaS
     op.s64 = b32.dev();
     op.sP = bin.dev();
     int nb = 0;
-    op.map = block_map(b32, BLAS_B, nb);
+    const int vb = vec_block(b32);
+    op.map = block_map(b32, vb, nb);
     op.a = const_cast<char*>(in);
     op.b = out;
     op.c = nullptr;
     op.sc = nullptr;
     ProfScope prof(PROF_OUTER, b32.sites() * (96.0 + spinor_bytes(bin.prec)), st);
-    if (bin.prec == P16) k_to_f32<P16><<<nb, BLAS_B, 0, st>>>(op);
-    else if (bin.prec == P32) k_to_f32<P32><<<nb, BLAS_B, 0, st>>>(op);
+    if (bin.prec == P16) k_to_f32<P16><<<nb, vb, 0, st>>>(op);
+    else if (bin.prec == P32) k_to_f32<P32><<<nb, vb, 0, st>>>(op);
     else throw Error(BPP_ERR_UNSUPPORTED, "to_f32 takes FP16 or FP32 vectors");
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -605,7 +630,8 @@ void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m3
     op.s64 = b64.dev();
     op.sP = b32.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     rb.ensure(nb, b64.nsys(), st);
     op.a = r_s;
     op.b = const_cast<char*>(m32);
@@ -614,7 +640,7 @@ void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m3
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
     ProfScope prof(PROF_OUTER, b64.sites() * (2 * 192.0 + 96.0), st);
-    k_defect_update<<<nb, BLAS_B, 0, st>>>(op);
+    k_defect_update<<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -676,13 +702,14 @@ static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, c
     op.s64 = b64.dev();
     op.sP = b64.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     op.a = a;
     op.b = b;
     op.c = nullptr;
     op.sc = sc;
     ProfScope prof(PROF_OUTER, bytes, st);
-    kern<<<nb, BLAS_B, 0, st>>>(op);
+    kern<<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -739,7 +766,8 @@ void odd_reconstruct(const Batch& b64, bool clover, const char* bo, const char* 
     op.s64 = b64.dev();
     op.sP = b64.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     rb.ensure(nb, b64.nsys(), st);
     op.a = const_cast<char*>(bo);
     op.b = const_cast<char*>(h);
@@ -748,8 +776,8 @@ void odd_reconstruct(const Batch& b64, bool clover, const char* bo, const char* 
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
     ProfScope prof(PROF_OUTER, b64.sites() * (3 * 192.0 + (clover ? 2 * 576.0 : 0.0)), st);
-    if (clover) k_odd_reconstruct<true><<<nb, BLAS_B, 0, st>>>(op);
-    else k_odd_reconstruct<false><<<nb, BLAS_B, 0, st>>>(op);
+    if (clover) k_odd_reconstruct<true><<<nb, vb, 0, st>>>(op);
+    else k_odd_reconstruct<false><<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -759,7 +787,8 @@ void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal*
     op.s64 = b64.dev();
     op.sP = b64.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     rb.ensure(nb, b64.nsys(), st);
     op.a = bhat_s;
     op.b = m_s;
@@ -768,7 +797,7 @@ void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r64, KScal*
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
     ProfScope prof(PROF_OUTER, b64.sites() * (m_s ? 3 : 2) * 192.0, st);
-    k_split_residual<<<nb, BLAS_B, 0, st>>>(op);
+    k_split_residual<<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -780,7 +809,8 @@ void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& 
     op.s64 = b64.dev();
     op.sP = b64.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     rb.ensure(nb, b64.nsys(), st);
     op.a = bhat;
     op.b = r64;
@@ -789,7 +819,7 @@ void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& 
     op.partials = rb.partials.as<double>();
     op.tickets = rb.tickets.as<unsigned>();
     ProfScope prof(PROF_OUTER, b64.sites() * 3 * 192.0, st);
-    k_outer_residual<<<nb, BLAS_B, 0, st>>>(op);
+    k_outer_residual<<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }
@@ -800,20 +830,21 @@ void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo
     op.s64 = b64.dev();
     op.sP = bP.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     op.a = const_cast<char*>(r64);
     op.b = lo;
     op.c = nullptr;
     op.sc = const_cast<KScal*>(sc);
     ProfScope prof(PROF_OUTER, b64.sites() * (192.0 + spinor_bytes(bP.prec)), st);
     if (split) {
-        if (bP.prec == P64) k_outer_down<P64, true><<<nb, BLAS_B, 0, st>>>(op);
-        else if (bP.prec == P32) k_outer_down<P32, true><<<nb, BLAS_B, 0, st>>>(op);
-        else k_outer_down<P16, true><<<nb, BLAS_B, 0, st>>>(op);
+        if (bP.prec == P64) k_outer_down<P64, true><<<nb, vb, 0, st>>>(op);
+        else if (bP.prec == P32) k_outer_down<P32, true><<<nb, vb, 0, st>>>(op);
+        else k_outer_down<P16, true><<<nb, vb, 0, st>>>(op);
     } else {
-        if (bP.prec == P64) k_outer_down<P64, false><<<nb, BLAS_B, 0, st>>>(op);
-        else if (bP.prec == P32) k_outer_down<P32, false><<<nb, BLAS_B, 0, st>>>(op);
-        else k_outer_down<P16, false><<<nb, BLAS_B, 0, st>>>(op);
+        if (bP.prec == P64) k_outer_down<P64, false><<<nb, vb, 0, st>>>(op);
+        else if (bP.prec == P32) k_outer_down<P32, false><<<nb, vb, 0, st>>>(op);
+        else k_outer_down<P16, false><<<nb, vb, 0, st>>>(op);
     }
     count_launch();
     BPP_CHECK_LAUNCH();
@@ -825,15 +856,16 @@ void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* 
     op.s64 = b64.dev();
     op.sP = bP.dev();
     int nb = 0;
-    op.map = block_map(b64, BLAS_B, nb);
+    const int vb = vec_block(b64);
+    op.map = block_map(b64, vb, nb);
     op.a = x64;
     op.b = const_cast<char*>(e);
     op.c = x_split;
     op.sc = const_cast<KScal*>(sc);
-    ProfScope prof(PROF_OUTER, b64.sites() * (2 * 192.0 + spinor_bytes(bP.prec) + (x_split ? 2 * 192.0 : 0.0)), st);
-    if (bP.prec == P64) k_outer_acc<P64><<<nb, BLAS_B, 0, st>>>(op);
-    else if (bP.prec == P32) k_outer_acc<P32><<<nb, BLAS_B, 0, st>>>(op);
-    else k_outer_acc<P16><<<nb, BLAS_B, 0, st>>>(op);
+    ProfScope prof(PROF_OUTER, b64.sites() * ((x64 ? 2 * 192.0 : 0.0) + spinor_bytes(bP.prec) + (x_split ? 2 * 192.0 : 0.0)), st);
+    if (bP.prec == P64) k_outer_acc<P64><<<nb, vb, 0, st>>>(op);
+    else if (bP.prec == P32) k_outer_acc<P32><<<nb, vb, 0, st>>>(op);
+    else k_outer_acc<P16><<<nb, vb, 0, st>>>(op);
     count_launch();
     BPP_CHECK_LAUNCH();
 }

@@ -78,7 +78,8 @@ void outer_residual(const Batch& b64, char* bhat, char* r64, KScal* sc, RedBuf& 
 void outer_downcast(const Batch& b64, const Batch& bP, const char* r64, char* lo, const KScal* sc, cudaStream_t st,
                     bool split = false);
 // x64 += scale * e (e in the inner precision); with x_split, also refresh the
-// split-FP64 copy of x (hi/lo FP32 pairs) used by the double-float defects
+// split-FP64 copy of x (hi/lo FP32 pairs) used by the double-float defects;
+// x64 may be null when the split copy is the only iterate
 void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* e, const KScal* sc, cudaStream_t st,
                       char* x_split = nullptr);
 // r_s = bhat_s - m_s in double-float (m_s may be null), split-FP64 output, with

@@ -150,6 +150,18 @@ __device__ __forceinline__ void decode(const Raw32c& r, cx<float> psi[12], cx<fl
     }
     third_row(u);
 }
+// a two-row FP32 link alone (the multi-RHS kernel loads each link once for
+// several right-hand sides; later groups of the batch find it in L2)
+__device__ __forceinline__ void load_link12(const LinkView& U, int64_t ju, cx<float> u[9]) {
+    const float4* q = static_cast<const float4*>(U.data);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 v = __ldg(q + k * U.stride + ju);
+        u[2 * k] = mkc(v.x, v.y);
+        u[2 * k + 1] = mkc(v.z, v.w);
+    }
+    third_row(u);
+}
 template <int P, bool C> struct RawSel { using type = Raw<P>; };
 template <> struct RawSel<P32, true> { using type = Raw32c; };
 
@@ -183,30 +195,39 @@ __device__ __forceinline__ void df_lazy_add(float& S, float& E, float p, float e
     E += ((S - (s - bb)) + (p - bb)) + e;
     S = s;
 }
+// One row of U (u[0..2]) times both colour vectors of h: g0 = u . h[0..2],
+// g1 = u . h[3..5].
+__device__ __forceinline__ void df_row(const cx<df64> u[3], const cx<df64> h[6], cx<df64>& g0, cx<df64>& g1) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f, p, e;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const cx<df64> x = h[3 * s + b];
+            // re += u.r x.r - u.i x.i
+            df_prod(u[b].r, x.r, p, e);
+            if (b == 0) { Sr = p; Er = e; } else df_lazy_add(Sr, Er, p, e);
+            df_prod(u[b].i, x.i, p, e);
+            df_lazy_add(Sr, Er, -p, -e);
+            // im += u.r x.i + u.i x.r
+            df_prod(u[b].r, x.i, p, e);
+            if (b == 0) { Si = p; Ei = e; } else df_lazy_add(Si, Ei, p, e);
+            df_prod(u[b].i, x.r, p, e);
+            df_lazy_add(Si, Ei, p, e);
+        }
+        (s == 0 ? g0 : g1) = mkc(quick_two_sum(Sr, Er), quick_two_sum(Si, Ei));
+    }
+}
+// g = U h, or U^dag h (rows of U^dag: conjugated columns of U)
 template <bool BACK>
 __device__ __forceinline__ void link_mul(const cx<df64> U[9], const cx<df64> h[6], cx<df64> g[6]) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int a = 0; a < 3; ++a) {
+        cx<df64> ur[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f, p, e;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const cx<df64> u = BACK ? U[3 * b + a] : U[3 * a + b];
-                const cx<df64> x = h[3 * s + b];
-                // re += u.r x.r - u.i x.i  (U^dag: + u.i x.i)
-                df_prod(u.r, x.r, p, e);
-                if (b == 0) { Sr = p; Er = e; } else df_lazy_add(Sr, Er, p, e);
-                df_prod(u.i, x.i, p, e);
-                if (BACK) df_lazy_add(Sr, Er, p, e); else df_lazy_add(Sr, Er, -p, -e);
-                // im += u.r x.i + u.i x.r  (U^dag: - u.i x.r)
-                df_prod(u.r, x.i, p, e);
-                if (b == 0) { Si = p; Ei = e; } else df_lazy_add(Si, Ei, p, e);
-                df_prod(u.i, x.r, p, e);
-                if (BACK) df_lazy_add(Si, Ei, -p, -e); else df_lazy_add(Si, Ei, p, e);
-            }
-            g[3 * s + a] = mkc(quick_two_sum(Sr, Er), quick_two_sum(Si, Ei));
-        }
+        for (int b = 0; b < 3; ++b) ur[b] = BACK ? mkc(U[3 * b + a].r, -U[3 * b + a].i) : U[3 * a + b];
+        df_row(ur, h, g[a], g[3 + a]);
+    }
 }
 
 template <int MU, int S, bool BACK, class RAW, class real>
@@ -216,6 +237,51 @@ __device__ __forceinline__ void hop_term(cx<real> acc[12], const RAW& raw, bool 
     hop_term_dec<MU, S, BACK>(acc, psi, u, flip);
 }
 
+// Element k of an 8-entry register array for a runtime k (a switch keeps the
+// array in registers; an indexed access would move it to local memory).
+template <class T>
+__device__ __forceinline__ T pick8(const T a[8], int k) {
+    switch (k) {
+        case 0: return a[0];
+        case 1: return a[1];
+        case 2: return a[2];
+        case 3: return a[3];
+        case 4: return a[4];
+        case 5: return a[5];
+        case 6: return a[6];
+        default: return a[7];
+    }
+}
+
+// Projection and reconstruction of direction d = 2 mu + back for a runtime d
+// (small code per case; used by the double-float hop, whose colour product is
+// too large to inline eight times).
+template <int SF, class real>
+__device__ __forceinline__ void project_rt(int d, const cx<real> psi[12], cx<real> h[6]) {
+    switch (d) {
+        case 0: project<0, SF>(psi, h); break;
+        case 1: project<0, -SF>(psi, h); break;
+        case 2: project<1, SF>(psi, h); break;
+        case 3: project<1, -SF>(psi, h); break;
+        case 4: project<2, SF>(psi, h); break;
+        case 5: project<2, -SF>(psi, h); break;
+        case 6: project<3, SF>(psi, h); break;
+        default: project<3, -SF>(psi, h); break;
+    }
+}
+template <int SF, class real>
+__device__ __forceinline__ void reconstruct_rt(int d, cx<real> acc[12], const cx<real> g[6]) {
+    switch (d) {
+        case 0: reconstruct<0, SF>(acc, g); break;
+        case 1: reconstruct<0, -SF>(acc, g); break;
+        case 2: reconstruct<1, SF>(acc, g); break;
+        case 3: reconstruct<1, -SF>(acc, g); break;
+        case 4: reconstruct<2, SF>(acc, g); break;
+        case 5: reconstruct<2, -SF>(acc, g); break;
+        case 6: reconstruct<3, SF>(acc, g); break;
+        default: reconstruct<3, -SF>(acc, g); break;
+    }
+}
 // Direction d with decoded operands (see hop_term_d).
 template <int SF, class real>
 __device__ __forceinline__ void hop_term_dec_d(int d, cx<real> acc[12], const cx<real> psi[12], const cx<real> u[9],
@@ -384,7 +450,44 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     // domain and are not used)
     const bool top = DD && x4 == g.L[3] - 1, bot = DD && x4 == 0;
     const int64_t fidx = DD ? (int64_t)i - (int64_t)g.Lh * g.L[1] * g.L[2] * x4 : 0;
-    if (HopPrefetch<P>::value) {
+    if constexpr (P == P64S) {
+        // one copy of the double-float colour product, the directions in a
+        // loop (eight inlined copies overflow the instruction cache), and the
+        // link read row by row (U) or column by column (U^dag) as it is used
+        const float4* sp = static_cast<const float4*>(in.data);
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            const bool back = k & 1;
+            const int64_t jk = pick8(jn, k), uk = pick8(ju, k);
+            cx<real> h[6], gk[6];
+            {
+                cx<real> psi[12];
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const float4 v = __ldg(sp + c * in.stride + jk);
+                    psi[c] = mkc(df64(v.x, v.y), df64(v.z, v.w));
+                }
+                project_rt<SF>(k, psi, h);
+            }
+            if (pick8(flip, k)) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) h[c] = -h[c];
+            }
+            const LinkView U = d.U[back ? q : p][k >> 1];
+            const float4* up = static_cast<const float4*>(U.data);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                cx<real> ur[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float4 v = __ldcs(up + (back ? 3 * c + a : 3 * a + c) * U.stride + uk);
+                    ur[c] = mkc(df64(v.x, v.y), back ? df64(-v.z, -v.w) : df64(v.z, v.w));
+                }
+                df_row(ur, h, gk[a], gk[3 + a]);
+            }
+            reconstruct_rt<SF>(k, acc, gk);
+        }
+    } else if (HopPrefetch<P>::value) {
         typename RawSel<P, C>::type cur, nxt;
         load_raw(cur, in, jn[0], d.U[p][0], ju[0]);
 #pragma unroll
@@ -441,7 +544,7 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
 // R right-hand sides of one gauge field per thread: each link is loaded once
 // into registers and applied to the R half spinors (systems s0 .. s0+R-1 of a
 // uniform batch whose systems share the links).  hp.map counts groups of R.
-template <int P, bool DAG, int MODE, int R>
+template <int P, bool DAG, int MODE, int R, bool C = false>
 __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
     using real = typename PT<P>::real;
     int grp, tile;
@@ -478,7 +581,8 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         cx<real> u[9];
-        Access<P>::load_link(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
+        if constexpr (C && P == P32) load_link12(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
+        else Access<P>::load_link(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             cx<real> psi[12];
@@ -568,7 +672,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
         k_hop<P, DAG, MODE><<<nb, B, 0, st>>>(hp);
     };
     // right-hand sides of one gauge field can share each link load in registers
-    bool shared = !dd && !b.comp && b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
+    bool shared = !dd && b.uniform && b.nsys() >= 2 && (P == P32 || P == P16);
     for (int s = 1; shared && s < b.nsys(); ++s) shared = b.sys[s].U[0][0].data == b.sys[0].U[0][0].data;
     auto run_multi = [&](int R, int B) {
         BlockMap m;
@@ -578,6 +682,13 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
         for (int t = 0; t <= MAXSYS; ++t) m.tile_start[t] = 0;
         hp.map = m;
         const int nb = m.tiles_per_sys * m.nsys;
+        if constexpr (P == P32) {
+            if (b.comp) {
+                if (R == 2) k_hop_multi<P, DAG, MODE, 2, true><<<nb, B, 0, st>>>(hp);
+                else k_hop_multi<P, DAG, MODE, 4, true><<<nb, B, 0, st>>>(hp);
+                return;
+            }
+        }
         if constexpr (P == P32 || P == P16) {
             if (R == 2) k_hop_multi<P, DAG, MODE, 2><<<nb, B, 0, st>>>(hp);
             else k_hop_multi<P, DAG, MODE, 4><<<nb, B, 0, st>>>(hp);

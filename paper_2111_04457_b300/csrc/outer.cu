@@ -52,15 +52,18 @@ __global__ void k_oc_full_odd(OuterDev* od, const KScal* s64, int n) {
 }
 
 // ... then the even part, whose norm stays in the scalars for the downcast of
-// a further correction.
-__global__ void k_oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64) {
+// a further correction.  split: the double-float check, whose even defect is
+// split-FP64 and whose odd half vanishes by construction (x_o is A_oo^-1 of
+// b_o + kappa H_oe x_e itself), so it is not recomputed.
+__global__ void k_oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64, int split) {
     if (threadIdx.x != 0) return;
     for (int s = 0; s < oc->n; ++s) {
         od[s].rr_e = s64[s].rr;
+        if (split) od[s].rr_o = 0.0;
         s64[s].scale = sqrt(fmax(od[s].rr_e, 0.0));
     }
     oc->have_full = 1;
-    oc->defect_split = 0;
+    oc->defect_split = split;
     oc->n_full += 1;
 }
 
@@ -156,8 +159,8 @@ void oc_classify(OuterDev* od, OuterCtl* oc, unsigned long long hc, unsigned lon
 void oc_full_odd(OuterDev* od, const KScal* s64, int n, cudaStream_t st) {
     OC_LAUNCH(k_oc_full_odd<<<1, 32, 0, st>>>(od, s64, n));
 }
-void oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64, cudaStream_t st) {
-    OC_LAUNCH(k_oc_full_even<<<1, 32, 0, st>>>(od, oc, s64));
+void oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64, cudaStream_t st, bool split) {
+    OC_LAUNCH(k_oc_full_even<<<1, 32, 0, st>>>(od, oc, s64, split ? 1 : 0));
 }
 void oc_inner_setup(OuterDev* od, OuterCtl* oc, KScal* s64, KScal* sP, unsigned long long hs, cudaStream_t st) {
     OC_LAUNCH(k_oc_inner_setup<<<1, 32, 0, st>>>(od, oc, s64, sP, hs));

@@ -34,7 +34,7 @@ enum OuterBranch { OB_FULL = 0, OB_RELIABLE = 1, OB_SCHUR = 2 };
 // Kernel launchers; a handle of 0 means "no graph: do not set a condition".
 void oc_classify(OuterDev* od, OuterCtl* oc, unsigned long long h_check, unsigned long long h_inner, cudaStream_t st);
 void oc_full_odd(OuterDev* od, const KScal* s64, int n, cudaStream_t st);
-void oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64, cudaStream_t st);
+void oc_full_even(OuterDev* od, OuterCtl* oc, KScal* s64, cudaStream_t st, bool split = false);
 void oc_inner_setup(OuterDev* od, OuterCtl* oc, KScal* s64, KScal* sP, unsigned long long h_split, cudaStream_t st);
 void oc_decide(OuterDev* od, OuterCtl* oc, const KScal* sP, unsigned long long h_branch, cudaStream_t st);
 void oc_after_reliable(OuterDev* od, OuterCtl* oc, const KScal* s64, cudaStream_t st);

@@ -81,6 +81,7 @@ struct Plan {
     bool clover = false;
     int prec = P32, solver = BPP_BICGSTAB;
     bool split = false;                  // double-float defects (split-FP64 vectors)
+    bool dfcheck = false;                // the true-residual check in double-float too (x split only)
     bool reliable = false;               // FP32 recursive defect updates between recomputations
     Batch b64, bP, b64s, b32;
     Vec e32, m32, tmp32;
@@ -120,7 +121,7 @@ static std::mutex g_plan_mu;
 static std::vector<std::unique_ptr<Plan>> g_plans;
 static uint64_t g_plan_clock = 0;
 static const size_t PLAN_BUDGET = (size_t)48 << 30;
-static const size_t MAX_PLANS = 4;
+static const size_t MAX_PLANS = 16;
 
 static void alloc_vec(Plan& pl, Vec& v, const Batch& b) {
     v.buf.alloc_persistent(b.vec_bytes);
@@ -128,11 +129,11 @@ static void alloc_vec(Plan& pl, Vec& v, const Batch& b) {
 }
 
 static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<double>& kappa, bool clover, int prec,
-                      int solver, bool split, cudaStream_t st) {
+                      int solver, bool split, bool dfcheck, cudaStream_t st) {
     ++g_plan_clock;
     for (auto& p : g_plans)
         if (p->G == G && p->kappa == kappa && p->clover == clover && p->prec == prec && p->solver == solver &&
-            p->split == split) {
+            p->split == split && p->dfcheck == dfcheck) {
             p->last_use = g_plan_clock;
             return *p;
         }
@@ -143,6 +144,7 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     pl->prec = prec;
     pl->solver = solver;
     pl->split = split;
+    pl->dfcheck = dfcheck;
     pl->b64.prec = P64;
     pl->bP.prec = prec;
     pl->b64s.prec = P64S;
@@ -441,11 +443,15 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     BPP_REQUIRE(o.solver == BPP_BICGSTAB || o.solver == BPP_CGNR, BPP_ERR_INVALID_ARG, "unknown solver");
     BPP_REQUIRE(o.inner_prec >= BPP_F64 && o.inner_prec <= BPP_F16, BPP_ERR_INVALID_ARG, "unknown inner precision");
     BPP_REQUIRE(o.max_inner > 0 && o.max_outer > 0 && o.check_every > 0, BPP_ERR_INVALID_ARG, "iteration caps must be positive");
+    BPP_REQUIRE(o.outer_arith >= 0 && o.outer_arith <= 2, BPP_ERR_INVALID_ARG, "outer_arith must be 0, 1 or 2");
 
     std::lock_guard<std::mutex> lk(g_plan_mu);
     // a plain FP64 solve (FP64 inner) stays FP64 throughout
     const bool split = o.outer_arith != 0 && o.inner_prec != BPP_F64;
-    Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, split, st);
+    // outer_arith 2: the true-residual check in double-float as well, the split
+    // copy of x the only iterate (returned as its exact FP64 value)
+    const bool dfcheck = split && o.outer_arith >= 2;
+    Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, split, dfcheck, st);
     const Batch& b64 = pl.b64;
     const Batch& bP = pl.bP;
     KScal* sc64 = pl.d64.as<KScal>();
@@ -522,6 +528,18 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
 
     // the branch kernel sequences (host-driven and captured alike)
     auto full_kernels = [&](cudaStream_t cs) {
+        if (dfcheck) {
+            // The same check in double-float arithmetic on the split iterate:
+            // x_o = A_oo^-1 (b_o + kappa H_oe x_e) in one hop (kept in tmpo_s
+            // for the returned x), De = A_ee x_e - kappa H_eo x_o, and the even
+            // residual b_e - De as the next split defect.  The odd residual
+            // vanishes by construction and is not recomputed.
+            hop(b64s, 1, dag, clover ? HOP_INV_XPAY : HOP_XPAY, +1.0, pl.xe_s.p(), pl.tmpo_s.p(), pl.bo_s.p(), cs);
+            hop(b64s, 0, dag, clover ? HOP_CLOV_XPAY : HOP_XPAY, -1.0, pl.tmpo_s.p(), pl.m_s.p(), pl.xe_s.p(), cs);
+            split_residual(b64, pl.be_s.p(), pl.m_s.p(), pl.r_s.p(), sc64, pl.rb, cs);
+            oc_full_even(od, oc, sc64, cs, true);
+            return;
+        }
         // The true residual of the returned x with the full FP64 D: h = kappa
         // H_oe x_e once, x_o = A_oo^-1 (b_o + h) and the odd residual
         // b_o - (A_oo x_o - h) from it, then De = A_ee x_e - kappa H_eo x_o and
@@ -659,7 +677,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                         }
                         pl.w_iter_launch = i2.launches - i1.launches;
                         pl.w_iter_hops = i2.hops[bP.prec] - i1.hops[bP.prec];
-                        outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, s2, split ? pl.xe_s.p() : nullptr);
+                        outer_accumulate(b64, bP, dfcheck ? nullptr : pl.xe.p(), pl.w[1].p(), sc64, s2, split ? pl.xe_s.p() : nullptr);
                         oc_decide(od, oc, scP, h_branch, s2);
                         const CapSnap i3 = cap_snap(n);
                         // both downcast variants were captured, one runs
@@ -729,7 +747,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
                 oc_inner_setup(od, oc, sc64, scP, 0, st);
                 downcast(hoc.defect_split != 0, st);
                 inner_solve(pl, o, st);
-                outer_accumulate(b64, bP, pl.xe.p(), pl.w[1].p(), sc64, st, split ? pl.xe_s.p() : nullptr);
+                outer_accumulate(b64, bP, dfcheck ? nullptr : pl.xe.p(), pl.w[1].p(), sc64, st, split ? pl.xe_s.p() : nullptr);
                 oc_decide(od, oc, scP, 0, st);
                 read_state();
                 if (hoc.branch == OB_FULL) full_kernels(st);
@@ -770,6 +788,11 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     } else {
         for (int s = 0; s < n; ++s)
             if (status[s] == BPP_OK && bnorm2[s] > 0.0) true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);
+    }
+    if (dfcheck) {
+        // the checked split iterate is the solution (hi + lo, exact in FP64)
+        split_to_f64(b64, pl.xe_s.p(), pl.xe.p(), st);
+        split_to_f64(b64, pl.tmpo_s.p(), pl.xo.p(), st);
     }
     // x = ||b|| x'
     for (int s = 0; s < n; ++s)

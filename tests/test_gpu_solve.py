@@ -105,10 +105,12 @@ def test_solve_nonfinite_input(lat):
 
 
 @pytest.mark.parametrize("inner", [0, 1, 2])
-@pytest.mark.parametrize("outer_df64", [False, True])
+@pytest.mark.parametrize("arith", [0, 1, 2])
 @pytest.mark.parametrize("csw", [0.0, 1.0])
-def test_solve_outer_arithmetic(inner, outer_df64, csw):
-    """Both outer-loop arithmetics reach the FP64 true residual (checked by the oracle)."""
+def test_solve_outer_arithmetic(inner, arith, csw):
+    """Every outer-loop arithmetic (all FP64; double-float defects with the FP64
+    check; double-float defects and check) reaches the true residual as the
+    oracle computes it, reports it to 5%, and agrees with the oracle's x."""
     bpp = lib()
     L = (4, 4, 6, 8)
     g, U = gauge(L)
@@ -116,9 +118,26 @@ def test_solve_outer_arithmetic(inner, outer_df64, csw):
     if csw:
         g.clover_build(KAPPA, csw)
         F = oracle.clover_field(U, KAPPA, csw, L)
-    b = synth.gaussian_spinor(L, seed=2)
-    x, st = bpp.solve(g, to_dev(b), KAPPA, csw, TOL, bpp.solve_opts(inner_prec=inner, outer_df64=outer_df64))
-    assert oracle.true_residual(U, b, to_np(x), KAPPA, L, BC, F) <= TOL
+    b = synth.gaussian_spinor(L, seed=2, nrhs=2)
+    x, st = bpp.solve(g, to_dev(b), KAPPA, csw, TOL, bpp.solve_opts(inner_prec=inner, outer_arith=arith))
+    x = to_np(x)
+    for r in range(2):
+        res = oracle.true_residual(U, b[r], x[r], KAPPA, L, BC, F)
+        assert res <= TOL and st[r]["converged"] == 1
+        assert abs(st[r]["true_resid"] - res) <= 0.05 * res + 1e-15
+        assert rel_err(x[r], oracle.solve(U, b[r], KAPPA, L, BC, F=F, tol=1e-13)) <= 1e-8
+
+
+def test_solve_outer_arith_rejects_bad_value(lat):
+    bpp = lib()
+    L, g, U, b = lat
+    o = bpp.solve_opts()
+    o.outer_arith = 3
+    with pytest.raises(bpp.BppError) as e:
+        bpp.solve(g, to_dev(b), KAPPA, 0.0, TOL, o)
+    assert e.value.code == -1
+    with pytest.raises(ValueError):
+        bpp.solve_opts(outer_arith=5)
 
 
 @pytest.mark.parametrize("scale", [1e-40, 1e-20, 1e20, 1e60])
