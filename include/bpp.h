@@ -233,11 +233,12 @@ typedef struct {
 
 /* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 0 (per precision),
  * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 2,
- * outer_arith 1. */
+ * outer_arith 2. */
 void bpp_solve_opts_default(bpp_solve_opts* opts);
 
 /* Solves D x = b (or D^dag x = b) for nrhs right-hand sides sharing the gauge
- * field, to a true FP64 residual ||b - D x|| / ||b|| <= tol per RHS, through
+ * field, to a true residual ||b - D x|| / ||b|| <= tol per RHS (D applied to
+ * the returned x in FP64 or, with outer_arith 2, in double-float), through
  * the even-odd Schur complement: bhat_e = b_e - D_eo D_oo^{-1} b_o,
  * Mhat x_e = bhat_e, x_o = D_oo^{-1}(b_o - D_oe x_e).
  * b, x: complex128 [nrhs][V][4][3], in device memory or in host memory (then
@@ -458,6 +459,16 @@ int bpp_work_read(int prec, int64_t* launches, double* bytes, int reset);
 
 /* Releases cached device workspace (synchronises the device). */
 int bpp_release_workspace(void);
+
+/* Measures the throughput of the FMA pipe of prec (BPP_F64 or BPP_F32) with a
+ * synthetic kernel (8 resp. 16 independent FMA chains per thread, 8 blocks of
+ * 256 threads per SM, best of 5 launches of tens of ms) and stores it in
+ * *tflops (an FMA counted as 2 flop).  The roofline denominator of the
+ * ALU-bound hopping kernels (the FP64 hop on the FP64 pipe, the double-float
+ * hop on the FP32 pipe), which the measurement of Sec. 3.3's kernels needs
+ * beside the memory bandwidth.  Synchronises `stream`.  Errors: INVALID_ARG,
+ * CUDA. */
+int bpp_fma_peak(int prec, double* tflops, bpp_stream stream);
 
 #ifdef __cplusplus
 }

@@ -100,6 +100,7 @@ _SIGS = {
     "bpp_prof_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), ctypes.POINTER(_d), _i], _i),
     "bpp_work_read": ([_i, ctypes.POINTER(_i64), ctypes.POINTER(_d), _i], _i),
     "bpp_release_workspace": ([], _i),
+    "bpp_fma_peak": ([_i, ctypes.POINTER(_d), _p], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -163,6 +164,13 @@ def work_read(prec: int, reset: bool = True):
 
 def release_workspace():
     _check(_lib.bpp_release_workspace())
+
+
+def fma_peak(prec: int, stream=None) -> float:
+    """Measured FMA-pipe throughput in TFLOP/s of prec (F64 or F32), bpp_fma_peak."""
+    t = ctypes.c_double()
+    _check(_lib.bpp_fma_peak(int(prec), ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 @dataclass(frozen=True)
@@ -318,7 +326,7 @@ def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000,
     intermediate defects in double-float arithmetic, the true-residual check and
     the solution accumulation in FP64; 2 the check and the iterate in
     double-float too (the returned x is the checked iterate's exact FP64 value).
-    None keeps the library default; outer_df64=False is outer_arith=0."""
+    None keeps the library default (2); outer_df64=False is outer_arith=0."""
     o = SolveOpts()
     _lib.bpp_solve_opts_default(ctypes.byref(o))
     o.solver = solver

@@ -270,7 +270,7 @@ void bpp_solve_opts_default(bpp_solve_opts* o) {
     o->dagger = 0;
     o->check_every = 4;
     o->use_graph = 2;
-    o->outer_arith = 1;
+    o->outer_arith = 2;
 }
 
 int bpp_solve(bpp_gauge U, const void* b, void* x, double kappa, double csw, double tol, int nrhs,
@@ -517,6 +517,14 @@ int bpp_prof_read(int prec, int64_t* launches, double* ms, double* bytes, int re
 
 int bpp_work_read(int prec, int64_t* launches, double* bytes, int reset) {
     return guard("bpp_work_read", [&]() -> int { return work_read(prec, launches, bytes, reset); });
+}
+
+int bpp_fma_peak(int prec, double* tflops, bpp_stream stream) {
+    return guard("bpp_fma_peak", [&]() -> int {
+        BPP_REQUIRE(tflops, BPP_ERR_INVALID_ARG, "tflops is NULL");
+        *tflops = fma_peak(prec, (cudaStream_t)stream);
+        return BPP_OK;
+    });
 }
 
 int bpp_release_workspace(void) {

@@ -474,4 +474,8 @@ int tuned_block(const std::string& key, cudaStream_t s, Run run, bool may_tune =
     return best_b;
 }
 
+// Measured FMA-pipe throughput (TFLOP/s, an FMA counted as 2 flop) of
+// prec = P64 or P32 (peak.cu).
+double fma_peak(int prec, cudaStream_t st);
+
 }  // namespace bpp

@@ -365,7 +365,13 @@ __device__ __forceinline__ void hop_neighbours(const Geom& g, int i, int x1, int
 }
 
 // FP64 needs more registers per thread than a 512-thread block allows.
-template <int P> struct HopMaxThreads { static constexpr int value = 512; };
+#ifndef BPP_HOP32_MAXT
+#define BPP_HOP32_MAXT 512
+#endif
+#ifndef BPP_HOP_MINB
+#define BPP_HOP_MINB 1
+#endif
+template <int P> struct HopMaxThreads { static constexpr int value = BPP_HOP32_MAXT; };
 template <> struct HopMaxThreads<P64> { static constexpr int value = 256; };
 template <> struct HopMaxThreads<P64S> { static constexpr int value = 256; };
 template <> struct HopMaxThreads<P16> { static constexpr int value = BPP_HOP16_MAXT; };
@@ -374,7 +380,8 @@ template <> struct HopMaxThreads<P16> { static constexpr int value = BPP_HOP16_M
 #ifndef BPP_HOPDF_MINB
 #define BPP_HOPDF_MINB 2
 #endif
-template <int P> struct HopMinBlocks { static constexpr int value = 1; };
+template <int P> struct HopMinBlocks { static constexpr int value = BPP_HOP_MINB; };
+template <> struct HopMinBlocks<P64> { static constexpr int value = 1; };
 template <> struct HopMinBlocks<P64S> { static constexpr int value = BPP_HOPDF_MINB; };
 
 // Face terms of a domain decomposition in x4 (see HopParams).  Forward hop at
@@ -458,10 +465,11 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
 #pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             const bool back = k & 1;
-            const int64_t jk = pick8(jn, k), uk = pick8(ju, k);
+            const int64_t uk = pick8(ju, k);
             cx<real> h[6], gk[6];
             {
                 cx<real> psi[12];
+                const int64_t jk = pick8(jn, k);
 #pragma unroll
                 for (int c = 0; c < 12; ++c) {
                     const float4 v = __ldg(sp + c * in.stride + jk);
@@ -694,10 +702,12 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
             else k_hop_multi<P, DAG, MODE, 4><<<nb, B, 0, st>>>(hp);
         }
     };
-    int R = 1;
+    int R = 1;   // right-hand sides per thread: 1 (k_hop), 2 or 4 (k_hop_multi)
     if (shared) {
-        R = tune_lookup(key + "R");
-        if (R <= 0 && may_tune && !capturing(st)) {
+        const int stored = tune_lookup(key + "R");
+        if (stored > 0) {
+            R = stored;
+        } else if (may_tune && !capturing(st)) {
             // time the R = 1, 2, 4 variants (each with its own block size) and keep the fastest
             cudaEvent_t e0, e1;
             BPP_CUDA(cudaEventCreate(&e0));
@@ -723,7 +733,6 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
             cudaEventDestroy(e1);
             tune_store(key + "R", R);
         }
-        if (R <= 0) R = 1;
     }
     const int B = R == 1 ? tuned_block(key, st, run, may_tune, HopMaxThreads<P>::value)
                          : tuned_block(key + "R" + std::to_string(R), st, [&](int Bx) { run_multi(R, Bx); }, may_tune, 256);

@@ -71,3 +71,16 @@ def test_prof_classes_without_gpu():
         with pytest.raises(bpp.BppError) as e:
             bpp.prof_read(c)
         assert e.value.code == -1
+
+
+def test_solve_opts_defaults_without_gpu():
+    """The documented defaults of bpp_solve_opts_default (header), read back
+    through the binding: BiCGStab, FP32 inner, per-precision inner tolerance,
+    whole-solve graph, double-float outer loop with its own check."""
+    import paper_2111_04457_b300 as bpp
+    o = bpp.SolveOpts()
+    bpp._lib.bpp_solve_opts_default(ctypes.byref(o))
+    assert (o.solver, o.inner_prec, o.inner_tol, o.max_inner, o.max_outer) == (bpp.BICGSTAB, bpp.F32, 0.0, 20000, 50)
+    assert (o.use_x0, o.dagger, o.check_every, o.use_graph, o.outer_arith) == (0, 0, 4, 2, 2)
+    assert bpp.solve_opts(outer_df64=False).outer_arith == 0
+    assert bpp.solve_opts(outer_arith=1).outer_arith == 1

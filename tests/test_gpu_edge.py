@@ -126,11 +126,13 @@ def test_error_paths():
     assert rel_err(out, oracle.hop_eo(U, to_np(x), KAPPA, L, 0, BC)) <= 1e-13
 
 
-def test_prof_classes_cover_the_solve():
+@pytest.mark.parametrize("arith", [1, 2])
+def test_prof_classes_cover_the_solve(arith):
     """With launch timing on, a host-driven mixed-precision solve credits the
-    hopping kernels of both precisions, the Krylov and outer-loop vector
-    kernels, the layout conversion and the control kernels, each with time and
-    (except control) algorithmic bytes."""
+    hopping kernels of the inner precision and the double-float outer loop (and
+    the FP64 hop of the true-residual check with outer_arith 1, none with 2),
+    the Krylov and outer-loop vector kernels, the layout conversion and the
+    control kernels, each with time and (except control) algorithmic bytes."""
     bpp = lib()
     L = (4, 4, 4, 8)
     g, U = gauge(L)
@@ -138,11 +140,13 @@ def test_prof_classes_cover_the_solve():
     bpp.prof_enable(True)
     for c in range(10):
         bpp.prof_read(c, reset=True)
-    bpp.solve(g, to_dev(b), KAPPA, 0.0, 1e-10, bpp.solve_opts(inner_prec=bpp.F32, use_graph=0))
+    bpp.solve(g, to_dev(b), KAPPA, 0.0, 1e-10, bpp.solve_opts(inner_prec=bpp.F32, use_graph=0, outer_arith=arith))
     bpp.prof_enable(False)
     got = {c: bpp.prof_read(c, reset=True) for c in range(10)}
-    for c in (0, 1, 3, 4, 5, 6, 7):
+    for c in ((0,) if arith == 1 else ()) + (1, 3, 4, 5, 6, 7):
         n, ms, by = got[c]
         assert n > 0 and ms > 0.0, (c, got[c])
         assert (by > 0.0) == (c != 7), (c, got[c])
+    if arith == 2:
+        assert got[0][0] == 0
     assert got[9][0] == 0
