@@ -209,11 +209,12 @@ typedef struct {
                          double-float too: x_o = A_oo^-1 (b_o + kappa H_oe x_e) and
                          the even residual b_e - (A_ee x_e - kappa H_eo x_o) are
                          computed in double-float (the odd residual vanishes by
-                         construction), and the returned x is the checked iterate's
-                         exact FP64 value.  The check's rounding error is of order
-                         1e-14 ||x|| / ||b|| relative, against the FP64 pipe's 1/64
-                         rate on this GPU.  Ignored (FP64) when inner_prec is F64;
-                         other values: INVALID_ARG */
+                         construction), and the returned x is the checked iterate
+                         (scaled back by ||b|| to ~1e-14).  The check's rounding error
+                         is of order 1e-14 ||x|| / ||b|| relative; it avoids the FP64
+                         pipe, which runs at 1/74 of the FP32 rate on this GPU
+                         (measured, bpp_fma_peak).  Ignored (FP64) when inner_prec is
+                         F64; other values: INVALID_ARG */
 } bpp_solve_opts;
 
 /* Per right-hand side statistics of a solve. */

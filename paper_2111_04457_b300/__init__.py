@@ -325,7 +325,7 @@ def solve_opts(solver=BICGSTAB, inner_prec=F32, inner_tol=None, max_inner=20000,
     outer_arith: 0 every outer-loop operator in FP64; 1 the preparation and the
     intermediate defects in double-float arithmetic, the true-residual check and
     the solution accumulation in FP64; 2 the check and the iterate in
-    double-float too (the returned x is the checked iterate's exact FP64 value).
+    double-float too (the returned x is the checked iterate).
     None keeps the library default (2); outer_df64=False is outer_arith=0."""
     o = SolveOpts()
     _lib.bpp_solve_opts_default(ctypes.byref(o))

@@ -42,7 +42,22 @@ struct df64 {
             lo = sign ? -l : l;
         }
     }
-    __device__ double to_double() const { return (double)hi + (double)lo; }
+    __device__ double to_double() const { return f2d(hi) + f2d(lo); }
+    // FP32 -> FP64 is exact: for normal numbers the FP64 pattern is the FP32
+    // one with the exponent rebiased (+1023 - 127) and the significand shifted
+    // up by 29 bits, built with integer operations (the FP64 pipe then carries
+    // only the one add of to_double); zero keeps its sign, subnormals,
+    // infinities and NaN take the hardware conversion.
+    static __device__ __forceinline__ double f2d(float f) {
+        const unsigned u = __float_as_uint(f);
+        const unsigned e = (u >> 23) & 0xFFu;
+        if (e == 0u && (u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+        if (e == 0u || e == 0xFFu) return (double)f;
+        const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                     ((unsigned long long)(e + 896u) << 52) |
+                                     ((unsigned long long)(u & 0x7FFFFFu) << 29);
+        return __longlong_as_double((long long)d);
+    }
 };
 
 __device__ __forceinline__ df64 quick_two_sum(float a, float b) {

@@ -588,14 +588,37 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
     constexpr int SF = DAG ? +1 : -1;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        cx<real> u[9];
-        if constexpr (C && P == P32) load_link12(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
-        else Access<P>::load_link(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
+        if constexpr (P == P16) {
+            // the raw FP16 link once; per right-hand side the same decode as
+            // the one-RHS kernel (the spinor's scale folded into the link), so
+            // the two forms give identical bits
+            Raw<P16> raw;
+            const uint4* lq = static_cast<const uint4*>(d0.U[(k & 1) ? q : p][k >> 1].data);
+            const int64_t ls = d0.U[(k & 1) ? q : p][k >> 1].stride;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            cx<real> psi[12];
-            Access<P>::load_spinor(sys_view<P>(hp.in, hp.sys[s0 + r]), jn[k], psi);
-            hop_term_dec_d<SF>(k, acc[r], psi, u, flip[k]);
+            for (int c = 0; c < 2; ++c) raw.u[c] = __ldg(lq + c * ls + ju[k]);
+            raw.u8 = __ldg(reinterpret_cast<const unsigned*>(lq + 2 * ls) + ju[k]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const SpinorView in = sys_view<P>(hp.in, hp.sys[s0 + r]);
+                const uint4* sp = static_cast<const uint4*>(in.data);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) raw.s[c] = __ldg(sp + c * in.stride + jn[k]);
+                raw.sc = __ldg(in.scale + jn[k]);
+                cx<real> psi[12], u[9];
+                decode(raw, psi, u);
+                hop_term_dec_d<SF>(k, acc[r], psi, u, flip[k]);
+            }
+        } else {
+            cx<real> u[9];
+            if constexpr (C && P == P32) load_link12(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
+            else Access<P>::load_link(d0.U[(k & 1) ? q : p][k >> 1], ju[k], u);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                cx<real> psi[12];
+                Access<P>::load_spinor(sys_view<P>(hp.in, hp.sys[s0 + r]), jn[k], psi);
+                hop_term_dec_d<SF>(k, acc[r], psi, u, flip[k]);
+            }
         }
     }
 #pragma unroll

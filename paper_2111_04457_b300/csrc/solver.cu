@@ -449,7 +449,7 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     // a plain FP64 solve (FP64 inner) stays FP64 throughout
     const bool split = o.outer_arith != 0 && o.inner_prec != BPP_F64;
     // outer_arith 2: the true-residual check in double-float as well, the split
-    // copy of x the only iterate (returned as its exact FP64 value)
+    // copy of x the only iterate (the returned solution)
     const bool dfcheck = split && o.outer_arith >= 2;
     Plan& pl = get_plan(G, kappa, clover, o.inner_prec, o.solver, split, dfcheck, st);
     const Batch& b64 = pl.b64;
@@ -789,14 +789,14 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         for (int s = 0; s < n; ++s)
             if (status[s] == BPP_OK && bnorm2[s] > 0.0) true_res[s] = std::sqrt((rr_e[s] + rr_o[s]) / bnorm2[s]);
     }
-    if (dfcheck) {
-        // the checked split iterate is the solution (hi + lo, exact in FP64)
-        split_to_f64(b64, pl.xe_s.p(), pl.xe.p(), st);
-        split_to_f64(b64, pl.tmpo_s.p(), pl.xo.p(), st);
+    // x = ||b|| x' (with the double-float check the checked split iterate is
+    // the solution: x_e, and x_o in tmpo_s, converted on the way out)
+    for (int s = 0; s < n; ++s) {
+        if (dfcheck)
+            eo_to_full(b64s, s, 1, pl.xe_s.p(), pl.tmpo_s.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st, bscale[s]);
+        else
+            eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st, bscale[s]);
     }
-    // x = ||b|| x'
-    for (int s = 0; s < n; ++s)
-        eo_to_full(b64, s, 1, pl.xe.p(), pl.xo.p(), x_canon[s], 1, 0, o.dagger ? 1 : 0, st, bscale[s]);
     BPP_CUDA(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     double work1 = 0.0;
