@@ -68,13 +68,24 @@ __global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, con
     cx<real> v[12];
     Access<P>::load_spinor(sys_view<P>(const_cast<char*>(p == 0 ? even : odd), d), i, v);
     TC* dst = canon + blockIdx.y * cstride + lex * 12;
-    if (scale != 1.0) {
-        const real f = (real)scale;
+    if constexpr (P == P64S) {
+        // split values convert to FP64 first and scale there: the scaled
+        // solution may lie outside the FP32 exponent range
 #pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = f * v[k];
+        for (int k = 0; k < 12; ++k) {
+            cx<double> w = mkc(v[k].r.to_double() * scale, v[k].i.to_double() * scale);
+            if (g5 && k < 6) w = -w;
+            dst[k] = to_canon<TC, double>(w);
+        }
+    } else {
+        if (scale != 1.0) {
+            const real f = (real)scale;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = f * v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>((g5 && k < 6) ? -v[k] : v[k]);
     }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>((g5 && k < 6) ? -v[k] : v[k]);
 }
 
 // Half fields: canonical [nsys][Vh][4][3] with system s at offset s*Vh*12.
