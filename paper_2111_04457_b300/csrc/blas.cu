@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(BLAS_B) k_scale_split(OuterParams op) {
     Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = f * v[k];
-    Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
+    if (op.c) Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
     if (op.b) {
         cx<df64> w[12];
 #pragma unroll
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(BLAS_B) k_f64_to_split(OuterParams op) {
 }
 
 static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, char* b, KScal* sc, double bytes,
-                         cudaStream_t st) {
+                         cudaStream_t st, char* c = nullptr) {
     OuterParams op;
     op.s64 = b64.dev();
     op.sP = b64.dev();
@@ -706,7 +706,7 @@ static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, c
     op.map = block_map(b64, vb, nb);
     op.a = a;
     op.b = b;
-    op.c = nullptr;
+    op.c = c;
     op.sc = sc;
     ProfScope prof(PROF_OUTER, bytes, st);
     kern<<<nb, vb, 0, st>>>(op);
@@ -718,8 +718,10 @@ void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) {
     launch_outer(k_scale_f64, b64, v, nullptr, sc, b64.sites() * 384.0, st);
 }
 
-void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st) {
-    launch_outer(k_scale_split, b64, v, out, sc, b64.sites() * (out ? 576.0 : 384.0), st);
+void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st, bool keep64) {
+    BPP_REQUIRE(keep64 || out, BPP_ERR_INVALID_ARG, "scale_split: nothing to write");
+    launch_outer(k_scale_split, b64, v, out, sc, b64.sites() * (192.0 + (keep64 ? 192.0 : 0.0) + (out ? 192.0 : 0.0)),
+                 st, keep64 ? v : nullptr);
 }
 
 void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st) {

@@ -89,8 +89,9 @@ void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r_s, KScal*
 void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st);
 // out = split-FP64 copy of the FP64 vector in
 void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st);
-// v *= sc[s].scale (FP64, in place) and, when out is given, out = its split-FP64 copy
-void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st);
+// v *= sc[s].scale (FP64, in place; not stored when keep64 is false) and, when
+// out is given, out = its split-FP64 copy
+void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st, bool keep64 = true);
 // out (FP32, batch b32) = in (FP16 or FP32, batch bin)
 void to_f32(const Batch& bin, const Batch& b32, const char* in, char* out, cudaStream_t st);
 // r_s -= scale * m32 (split-FP64 defect, FP32 m = Mhat e), with the new

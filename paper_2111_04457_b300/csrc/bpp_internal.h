@@ -404,6 +404,7 @@ const std::vector<double>& capture_work_bytes(int prec);
 int64_t capture_launches();
 // True while `s` is being captured into a CUDA graph.
 bool capturing(cudaStream_t s);
+
 // Chooses the block size for a launch identified by `key` (kernel + shape).
 // On the first call outside graph capture it times each candidate with CUDA
 // events through `run(block)` and keeps the fastest; `run` must be a pure

@@ -16,6 +16,14 @@
 
 namespace bpp {
 
+// The FP64 route of the split for magnitudes outside 2^-74 .. 2^100, kept
+// out of line so that the compiler does not if-convert it into every split
+// (its FP64 conversions would then occupy the slow FP64 pipe for all values).
+static __device__ __noinline__ void split_rare(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
 struct df64 {
     float hi, lo;
     __host__ __device__ df64() {}
@@ -32,8 +40,7 @@ struct df64 {
         if ((b << 1) == 0ULL) {
             hi = lo = __uint_as_float((unsigned)(b >> 32));   // +-0
         } else if (e < 949 || e > 1023 + 100) {
-            hi = __double2float_rn(v);
-            lo = __double2float_rn(v - (double)hi);
+            split_rare(v, hi, lo);
         } else {
             const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
             hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
@@ -43,19 +50,22 @@ struct df64 {
         }
     }
     __device__ double to_double() const { return f2d(hi) + f2d(lo); }
-    // FP32 -> FP64 is exact: for normal numbers the FP64 pattern is the FP32
-    // one with the exponent rebiased (+1023 - 127) and the significand shifted
-    // up by 29 bits, built with integer operations (the FP64 pipe then carries
-    // only the one add of to_double); zero keeps its sign, subnormals,
-    // infinities and NaN take the hardware conversion.
+    // FP32 -> FP64 is exact; the FP64 pattern is built with integer
+    // operations only (the FP64 pipe then carries just the one add of
+    // to_double): normal numbers rebias the exponent (+1023 - 127) and shift
+    // the significand up by 29 bits; subnormals are normalised with a count
+    // of leading zeros; zero keeps its sign; infinities and NaN get the
+    // all-ones exponent.  Branch-free (selects), so no FP64 conversion is
+    // issued on any path.
     static __device__ __forceinline__ double f2d(float f) {
         const unsigned u = __float_as_uint(f);
         const unsigned e = (u >> 23) & 0xFFu;
-        if (e == 0u && (u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
-        if (e == 0u || e == 0xFFu) return (double)f;
+        const unsigned m = u & 0x7FFFFFu;
+        const int lz = __clz(m) - 8;   // subnormal: shift bringing the leading one to bit 23
+        const unsigned mn = e == 0u ? ((m << lz) & 0x7FFFFFu) : m;
+        const unsigned en = e == 0u ? (m == 0u ? 0u : (unsigned)(897 - lz)) : (e == 0xFFu ? 2047u : e + 896u);
         const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                     ((unsigned long long)(e + 896u) << 52) |
-                                     ((unsigned long long)(u & 0x7FFFFFu) << 29);
+                                     ((unsigned long long)en << 52) | ((unsigned long long)mn << 29);
         return __longlong_as_double((long long)d);
     }
 };

@@ -485,8 +485,9 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
         h64[s].scale = 1.0 / bscale[s];
     }
     write_scalars(pl.d64, h64, st);
-    scale_split(b64, pl.be.p(), split ? pl.be_s.p() : nullptr, sc64, st);
-    scale_split(b64, pl.bo.p(), split ? pl.bo_s.p() : nullptr, sc64, st);
+    // (with the double-float check only the split copies of b are read later)
+    scale_split(b64, pl.be.p(), split ? pl.be_s.p() : nullptr, sc64, st, !dfcheck);
+    scale_split(b64, pl.bo.p(), split ? pl.bo_s.p() : nullptr, sc64, st, !dfcheck);
     // bhat = b_e + kappa H_eo A_oo^-1 b_o (double-float when split)
     {
         const Batch& bb = split ? b64s : b64;
@@ -506,9 +507,9 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     bool x_zero = !o.use_x0;
     if (o.use_x0) {
         for (int s = 0; s < n; ++s) full_to_eo(b64, s, 1, x_canon[s], 1, 0, pl.xe.p(), pl.xo.p(), o.dagger ? 1 : 0, st);
-        scale_split(b64, pl.xe.p(), split ? pl.xe_s.p() : nullptr, sc64, st);
+        scale_split(b64, pl.xe.p(), split ? pl.xe_s.p() : nullptr, sc64, st, !dfcheck);
     } else {
-        BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
+        if (!dfcheck) BPP_CUDA(cudaMemsetAsync(pl.xe.p(), 0, b64.vec_bytes, st));
         if (split) BPP_CUDA(cudaMemsetAsync(pl.xe_s.p(), 0, b64s.vec_bytes, st));
     }
 
