@@ -783,6 +783,14 @@ def workload_results(name, dev, steps, warm):
         work_bytes()
         ms, gU = _timed(step, steps, warm, stream)
         by = work_bytes() / (steps + warm)
+        # per-class time of one more step (the link-gradient kernel is class 9)
+        bpp.prof_enable(True)
+        for c in CLASS_NAMES:
+            bpp.prof_read(c, reset=True)
+        step()
+        torch.cuda.synchronize()
+        bpp.prof_enable(False)
+        budget = step_budget(bpp, measured_peaks()[0])
         import oracle
         t0 = time.perf_counter()
         x_o = oracle.solve(U_np, b_np, KAPPA, L, tol=1e-12)
@@ -793,6 +801,7 @@ def workload_results(name, dev, steps, warm):
         out = {"workload": "L = Re<eta, D^-1 b> on 16^3x32 FP64: forward solve, adjoint solve, recomputed x, "
                            "link-gradient kernel",
                "ms_per_step": ms, "gbs": by / (ms / 1e3) / 1e9, "grad_U_rel_err_vs_oracle": err,
+               "force_kernel_ms": budget["classes"].get("force", {}).get("ms"), "step_budget": budget,
                "oracle_s": cpu_s, "oracle_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
     elif name == "mg16":
         # multigrid-preconditioned GCR (FP32, FP64 defect correction) against
@@ -810,13 +819,34 @@ def workload_results(name, dev, steps, warm):
         ms, st = _timed(lambda: mg.solve(b, TOL, o)[1], steps, warm, stream)
         ol = bpp.solve_opts(inner_prec=bpp.F32)
         ms_l, st_l = _timed(lambda: bpp.solve_lex(g, b, KAPPA, 0.0, TOL, bpp.LEX_D, ol)[1], steps, warm, stream)
-        out = {"workload": "16^3x32 Wilson, kappa 0.12, one Gaussian RHS: two-level multigrid (4^4 blocks, 6 "
-                           "near-null vectors from one inverse-iteration pass) preconditioning flexible GCR in FP32 "
-                           "under FP64 defect correction, against lexical BiCGStab (FP32 inner, same outer loop)",
+        oe = bpp.solve_opts(inner_prec=bpp.F32)
+        ms_e, st_e = _timed(lambda: bpp.solve(g, b, KAPPA, 0.0, TOL, oe)[1], steps, warm, stream)
+        del mg
+        # near the critical kappa of smoother links (exp(i 0.1 H)): the regime
+        # where the coarse correction pays in iterations (one timed solve each)
+        U1 = torch.from_numpy(synth.random_links(L, seed=1, eps=0.1)).to(dev)
+        g1 = bpp.Gauge(U1, L)
+        kc = 0.127
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mg1 = bpp.Multigrid(g1, kc, vecs, (4, 4, 4, 4), refine=3)
+        torch.cuda.synchronize()
+        setup1 = 1000 * (time.perf_counter() - t0)
+        ms1, st1 = _timed(lambda: mg1.solve(b, TOL, o)[1], 1, 1, stream)
+        ms1e, st1e = _timed(lambda: bpp.solve(g1, b, kc, 0.0, TOL, oe)[1], 1, 3, stream)
+        del mg1, g1, U1
+        out = {"workload": "16^3x32 Wilson, one Gaussian RHS: two-level multigrid (4^4 blocks, 6 near-null vectors "
+                           "refined by inverse iteration) preconditioning flexible GCR in FP32 under FP64 defect "
+                           "correction, against lexical and even-odd BiCGStab (FP32 inner); at kappa 0.12 (links "
+                           "exp(i 0.3 H)) and near the critical kappa (links exp(i 0.1 H), kappa 0.127)",
                "ms_per_step": ms, "gbs": 0.0, "setup_ms": setup_ms, "gcr_iters": st[0]["inner_iters"],
                "true_resid": st[0]["true_resid"], "lex_bicgstab_ms": ms_l,
-               "lex_bicgstab_iters": st_l[0]["inner_iters"], "lex_true_resid": st_l[0]["true_resid"]}
-        del mg
+               "lex_bicgstab_iters": st_l[0]["inner_iters"], "lex_true_resid": st_l[0]["true_resid"],
+               "eo_bicgstab_ms": ms_e, "eo_bicgstab_iters": st_e[0]["inner_iters"],
+               "near_critical": {"kappa": kc, "link_eps": 0.1, "mg_setup_ms": setup1, "mg_ms": ms1,
+                                 "mg_gcr_iters": st1[0]["inner_iters"], "mg_true_resid": st1[0]["true_resid"],
+                                 "eo_bicgstab_ms": ms1e, "eo_bicgstab_iters": st1e[0]["inner_iters"],
+                                 "eo_true_resid": st1e[0]["true_resid"]}}
     elif name == "dd16":
         # the decomposed FP64 solve (slabs in x4 on this GPU) against the
         # undecomposed FP64 solve, 16^3x32
