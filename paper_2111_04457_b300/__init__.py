@@ -202,6 +202,17 @@ class Gauge:
         _check(_lib.bpp_gauge_create(ctypes.byref(lat), _ptr(U), _stream(stream), ctypes.byref(h)))
         self._h = h
         self.clover = None
+        # a few links of the source field, for matches() (a check, not a copy)
+        V = self.lattice.V
+        self._probe_sites = torch.tensor(sorted({0, V // 3, V // 2, (2 * V) // 3, V - 1}), dtype=torch.long)
+        self._probe = U[:, self._probe_sites.to(U.device)].detach().to("cpu", copy=True)
+
+    def matches(self, U: torch.Tensor) -> bool:
+        """True when U has this field's shape and equals its source field at the
+        probe sites (catches a gauge handle built from another field)."""
+        if U.dtype != torch.complex128 or tuple(U.shape) != (4, self.lattice.V, 3, 3):
+            return False
+        return bool(torch.equal(U.detach()[:, self._probe_sites.to(U.device)].cpu(), self._probe))
 
     @property
     def handle(self):

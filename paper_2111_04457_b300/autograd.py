@@ -57,9 +57,16 @@ def solve_fn(U: torch.Tensor, b: torch.Tensor, L, kappa: float, csw: float = 0.0
     """x = D[U]^{-1} b with gradients for b and U (Wilson or Wilson-clover).
 
     U: complex128 [4][V][3][3] CUDA tensor; b: complex128 [V][4][3] or [nrhs][V][4][3].
-    gauge: optional prebuilt Gauge for U (with its clover term if csw != 0)."""
+    gauge: optional prebuilt Gauge for U (with its clover term if csw != 0); it is
+    checked against U at a few probe sites and refused (ValueError) if it was
+    built from another field."""
     if gauge is None:
         gauge = Gauge(U.detach(), L, bc)
         if csw != 0.0:
             gauge.clover_build(kappa, csw)
+    else:
+        if U is not None and not gauge.matches(U):
+            raise ValueError("gauge was not built from U")
+        if csw != 0.0 and gauge.clover != (float(kappa), float(csw)):
+            raise ValueError("gauge's clover term was not built with this kappa and csw")
     return SolveFn.apply(U, b, gauge, float(kappa), float(csw), float(tol), int(inner_prec), bool(recompute))

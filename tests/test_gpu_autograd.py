@@ -147,3 +147,21 @@ def test_autograd_clover_fd_4x4():
             fd = (loss_c(to_dev(Up), b) - loss_c(to_dev(Um), b)) / (2 * h)
             an = np.trace(T @ P[mu, s]).real
             assert abs(float(fd) - an) <= 1e-6 * max(abs(an), 1e-2)
+
+
+def test_solve_fn_refuses_a_gauge_of_another_field():
+    """A prebuilt gauge handle must come from the U it is passed with (the
+    gradient would otherwise be the gradient of another field's solve)."""
+    bpp = lib()
+    from paper_2111_04457_b300.autograd import solve_fn
+    L = (4, 4, 4, 4)
+    U = synth.random_links(L, seed=1)
+    U2 = synth.random_links(L, seed=11)
+    g = bpp.Gauge(to_dev(U), L)
+    b = to_dev(synth.gaussian_spinor(L, seed=2))
+    x = solve_fn(to_dev(U), b, L, KAPPA, gauge=g)          # same field: accepted
+    assert x.shape == b.shape
+    with pytest.raises(ValueError):
+        solve_fn(to_dev(U2), b, L, KAPPA, gauge=g)
+    with pytest.raises(ValueError):
+        solve_fn(to_dev(U), b, L, KAPPA, csw=1.0, gauge=g)   # no clover term built
