@@ -458,10 +458,10 @@ int bpp_dd_solve(bpp_dd dd, const void* b, void* x, double kappa, double tol, in
 
 void bpp_mg_params_default(bpp_mg_params* p) {
     if (!p) return;
-    p->nu_pre = 2;
-    p->nu_post = 2;
-    p->coarse_tol = 0.05;
-    p->coarse_maxiter = 100;
+    p->nu_pre = 4;
+    p->nu_post = 4;
+    p->coarse_tol = 0.2;
+    p->coarse_maxiter = 15;
     p->gcr_restart = 12;
     p->setup_tol = 0.05;
 }

@@ -320,12 +320,18 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MGGeom m, const float2* P, 
     }
 }
 
-// out = D_c in, one thread per (coarse site, system)
-__global__ void k_mg_coarse_apply(MGGeom m, const float2* Dc, const char* in, char* out, const SysDesc* csys,
-                                  const int* done, int ds) {
+// out = D_c in, one thread per (coarse site, output component, system)
+__global__ void __launch_bounds__(384) k_mg_coarse_apply(MGGeom m, const float2* Dc, const char* in, char* out,
+                                                          const SysDesc* csys, const int* done, int ds) {
+    // one thread per (coarse site, output component r): the coarse lattice
+    // is small (Vc = V / block volume), so a thread per site would leave most
+    // SMs idle; the warps run over 32 consecutive coarse sites, so the D_c
+    // planes (site fastest) stay coalesced, and the 12 component warps of a
+    // block share the neighbour loads through L1
     const int s = blockIdx.y;
     if (done && done[s * ds]) return;
-    const int64_t B = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = threadIdx.y;
+    const int64_t B = (int64_t)blockIdx.x * 32 + threadIdx.x;
     if (B >= m.Vc) return;
     int b[4];
     {
@@ -334,9 +340,9 @@ __global__ void k_mg_coarse_apply(MGGeom m, const float2* Dc, const char* in, ch
         b[1] = (int)(t % m.Lc[1]); t /= m.Lc[1];
         b[2] = (int)(t % m.Lc[2]); b[3] = (int)(t / m.Lc[2]);
     }
-    cx<float> acc[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) acc[q] = mkc(0.f, 0.f);
+    const SpinorView vin = sys_view<P32>(const_cast<char*>(in), csys[s]);
+    const float4* vp = static_cast<const float4*>(vin.data);
+    cx<float> acc = mkc(0.f, 0.f);
     for (int term = 0; term < 9; ++term) {
         int nb[4] = {b[0], b[1], b[2], b[3]};
         if (term > 0) {
@@ -344,17 +350,19 @@ __global__ void k_mg_coarse_apply(MGGeom m, const float2* Dc, const char* in, ch
             nb[mu] = ((term - 1) & 1) ? (b[mu] - 1 + m.Lc[mu]) % m.Lc[mu] : (b[mu] + 1) % m.Lc[mu];
         }
         const int64_t Bn = nb[0] + (int64_t)m.Lc[0] * (nb[1] + (int64_t)m.Lc[1] * (nb[2] + (int64_t)m.Lc[2] * nb[3]));
-        cx<float> v[12];
-        Access<P32>::load_spinor(sys_view<P32>(const_cast<char*>(in), csys[s]), Bn, v);
+        const float2* row = Dc + (int64_t)(term * 144 + r * 12) * m.Sc + B;
 #pragma unroll
-        for (int r = 0; r < 12; ++r)
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                const float2 a = __ldg(Dc + (int64_t)(term * 144 + r * 12 + c) * m.Sc + B);
-                cfma(acc[r], mkc(a.x, a.y), v[c]);
-            }
+        for (int c2 = 0; c2 < 6; ++c2) {
+            const float4 w = __ldg(vp + c2 * vin.stride + Bn);
+            const float2 a0 = __ldg(row + (int64_t)(2 * c2) * m.Sc);
+            const float2 a1 = __ldg(row + (int64_t)(2 * c2 + 1) * m.Sc);
+            cfma(acc, mkc(a0.x, a0.y), mkc(w.x, w.y));
+            cfma(acc, mkc(a1.x, a1.y), mkc(w.z, w.w));
+        }
     }
-    Access<P32>::store_spinor(sys_view<P32>(out, csys[s]), B, acc);
+    float2* op = reinterpret_cast<float2*>(static_cast<float4*>(sys_view<P32>(out, csys[s]).data) +
+                                           (int64_t)(r >> 1) * csys[s].stride + B) + (r & 1);
+    *op = make_float2(acc.r, acc.i);
 }
 
 // y = coef_s x (mode 0) or y += coef_s x (mode 1), per system coefficients
@@ -478,11 +486,11 @@ struct MGRun {
     }
     void coarse_apply(const char* in, char* out, cudaStream_t st) {
         const MGGeom& m = mg.geom;
-        dim3 grid((unsigned)((m.Vc + 127) / 128), n);
+        dim3 grid((unsigned)((m.Vc + 31) / 32), n);
         const KScal* k = kc.as<KScal>();
         ProfScope prof(PROF_OUTER, (double)n * m.Vc * (9 * 96.0 + 9 * 144 * 8 + 96), st);
-        k_mg_coarse_apply<<<grid, 128, 0, st>>>(m, mg.Dc.as<float2>(), in, out, cb.dev(), &k[0].done,
-                                                (int)(sizeof(KScal) / sizeof(int)));
+        k_mg_coarse_apply<<<grid, dim3(32, 12), 0, st>>>(m, mg.Dc.as<float2>(), in, out, cb.dev(), &k[0].done,
+                                                         (int)(sizeof(KScal) / sizeof(int)));
         count_launch();
         BPP_CHECK_LAUNCH();
     }
