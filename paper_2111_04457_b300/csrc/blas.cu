@@ -522,38 +522,6 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
     }
 }
 
-// FP64 copy (hi + lo, exact) of a split-FP64 vector.
-__global__ void __launch_bounds__(BLAS_B) k_split_to_f64(OuterParams op) {
-    int s, tile;
-    map_block(op.map, s, tile);
-    const SysDesc& d = op.s64[s];
-    const int i = tile * blockDim.x + threadIdx.x;
-    if (i >= d.g.Vh) return;
-    cx<df64> v[12];
-    cx<double> w[12];
-    Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) w[k] = mkc(v[k].r.to_double(), v[k].i.to_double());
-    Access<P64>::store_spinor(sys_view<P64>(op.b, d), i, w);
-}
-
-void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st) {
-    OuterParams op;
-    op.s64 = b64.dev();
-    op.sP = b64.dev();
-    int nb = 0;
-    const int vb = vec_block(b64);
-    op.map = block_map(b64, vb, nb);
-    op.a = const_cast<char*>(xs);
-    op.b = x64;
-    op.c = nullptr;
-    op.sc = nullptr;
-    ProfScope prof(PROF_OUTER, b64.sites() * 384.0, st);
-    k_split_to_f64<<<nb, vb, 0, st>>>(op);
-    count_launch();
-    BPP_CHECK_LAUNCH();
-}
-
 // Copy of an inner-precision vector (op.a, batch sP) as FP32 (op.b, batch s64
 // holds the FP32 batch here).
 template <int PIN>
@@ -645,20 +613,6 @@ void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m3
     BPP_CHECK_LAUNCH();
 }
 
-// v *= scale of the system (FP64, in place).
-__global__ void __launch_bounds__(BLAS_B) k_scale_f64(OuterParams op) {
-    int s, tile;
-    map_block(op.map, s, tile);
-    const SysDesc& d = op.s64[s];
-    const int i = tile * blockDim.x + threadIdx.x;
-    if (i >= d.g.Vh) return;
-    const double f = op.sc[s].scale;
-    cx<double> v[12];
-    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = f * v[k];
-    Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
-}
 
 // v (op.a) *= scale in place (FP64) and op.b = its split-FP64 copy (op.b may be null).
 __global__ void __launch_bounds__(BLAS_B) k_scale_split(OuterParams op) {
@@ -681,20 +635,6 @@ __global__ void __launch_bounds__(BLAS_B) k_scale_split(OuterParams op) {
     }
 }
 
-// split-FP64 copy (op.b) of an FP64 vector (op.a).
-__global__ void __launch_bounds__(BLAS_B) k_f64_to_split(OuterParams op) {
-    int s, tile;
-    map_block(op.map, s, tile);
-    const SysDesc& d = op.s64[s];
-    const int i = tile * blockDim.x + threadIdx.x;
-    if (i >= d.g.Vh) return;
-    cx<double> v[12];
-    cx<df64> w[12];
-    Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) w[k] = mkc(df64(v[k].r), df64(v[k].i));
-    Access<P64S>::store_spinor(sys_view<P64S>(op.b, d), i, w);
-}
 
 static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, char* b, KScal* sc, double bytes,
                          cudaStream_t st, char* c = nullptr) {
@@ -714,18 +654,10 @@ static void launch_outer(void (*kern)(OuterParams), const Batch& b64, char* a, c
     BPP_CHECK_LAUNCH();
 }
 
-void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st) {
-    launch_outer(k_scale_f64, b64, v, nullptr, sc, b64.sites() * 384.0, st);
-}
-
 void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st, bool keep64) {
     BPP_REQUIRE(keep64 || out, BPP_ERR_INVALID_ARG, "scale_split: nothing to write");
     launch_outer(k_scale_split, b64, v, out, sc, b64.sites() * (192.0 + (keep64 ? 192.0 : 0.0) + (out ? 192.0 : 0.0)),
                  st, keep64 ? v : nullptr);
-}
-
-void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st) {
-    launch_outer(k_f64_to_split, b64, const_cast<char*>(in), out, nullptr, b64.sites() * 384.0, st);
 }
 
 // Odd half of the final check, all FP64: with h = kappa H_oe x_e (op.b) and

@@ -85,10 +85,6 @@ void outer_accumulate(const Batch& b64, const Batch& bP, char* x64, const char* 
 // r_s = bhat_s - m_s in double-float (m_s may be null), split-FP64 output, with
 // sc.rr = ||r_s||^2 and sc.scale = ||r_s||
 void split_residual(const Batch& b64, char* bhat_s, char* m_s, char* r_s, KScal* sc, RedBuf& rb, cudaStream_t st);
-// v *= sc[s].scale per system (FP64, in place)
-void scale_f64(const Batch& b64, char* v, KScal* sc, cudaStream_t st);
-// out = split-FP64 copy of the FP64 vector in
-void f64_to_split(const Batch& b64, const char* in, char* out, cudaStream_t st);
 // v *= sc[s].scale (FP64, in place; not stored when keep64 is false) and, when
 // out is given, out = its split-FP64 copy
 void scale_split(const Batch& b64, char* v, char* out, KScal* sc, cudaStream_t st, bool keep64 = true);
@@ -102,9 +98,5 @@ void defect_update(const Batch& b64, const Batch& b32, char* r_s, const char* m3
 // (b_o + h) written, ||b_o - (A_oo x_o - h)||^2 into sc.rr
 void odd_reconstruct(const Batch& b64, bool clover, const char* bo, const char* h, char* xo, KScal* sc, RedBuf& rb,
                      cudaStream_t st);
-// x64 = hi + lo of the split-FP64 vector xs (exact)
-void split_to_f64(const Batch& b64, const char* xs, char* x64, cudaStream_t st);
-// out = a * in + y (same precision), a per system given on the host
-void axpy_copy(const Batch& b, const char* in, char* out, cudaStream_t st);
 
 }  // namespace bpp
