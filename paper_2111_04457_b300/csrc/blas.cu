@@ -366,6 +366,75 @@ void blas_fin(int op, KScal* sc, const double* tot, int n, cudaStream_t st) {
     BPP_CHECK_LAUNCH();
 }
 
+// Sum of one system's per-warp partials of a fused hop (see hop_red_fin) in
+// two fixed levels: block c of system s sums partials [c RF_CH, (c+1) RF_CH)
+// (thread t adds t, t + RF_B, ... in order, then the warps' and the block's
+// sums in order) into a chunk sum; the last block of the system, found with a
+// ticket, adds the chunk sums in chunk order and derives alpha or omega.  The
+// grouping depends only on the lattice.
+constexpr int RF_B = 256;
+constexpr int RF_CH = 8 * RF_B;
+template <int OP>
+__global__ void __launch_bounds__(RF_B) k_hop_red_fin(const SysDesc* sys, KScal* sc, const double* part, int wstride,
+                                                      double* chunks, int chunk_stride, unsigned* tickets) {
+    const int s = blockIdx.y, c = blockIdx.x;
+    KScal& K = sc[s];
+    if (K.done) return;
+    const int nw = (sys[s].g.Vh + 31) >> 5;
+    const int nch = (nw + RF_CH - 1) / RF_CH;
+    if (c >= nch) return;
+    const double* p = part + (size_t)s * wstride * 4;
+    double a[3] = {0.0, 0.0, 0.0};
+    const int w1 = min(nw, (c + 1) * RF_CH);
+    for (int w = c * RF_CH + threadIdx.x; w < w1; w += RF_B) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] += p[4 * w + k];
+    }
+    __shared__ double sh[RF_B / 32][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double b = a[k];
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+        if (lane == 0) sh[warp][k] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double* cs = chunks + ((size_t)s * chunk_stride + c) * 4;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double b = 0.0;
+        for (int w = 0; w < RF_B / 32; ++w) b += sh[w][k];
+        cs[k] = b;
+    }
+    __threadfence();
+    if (atomicAdd(&tickets[s], 1u) != (unsigned)(nch - 1)) return;
+    __threadfence();
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    const double* c0 = chunks + (size_t)s * chunk_stride * 4;
+    for (int j = 0; j < nch; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tot[k] += __ldcg(&c0[4 * j + k]);
+    tickets[s] = 0u;
+    blas_finalize<OP>(K, tot);
+}
+
+int hop_red_chunks(int wstride) { return (wstride + RF_CH - 1) / RF_CH; }
+
+void hop_red_fin(const Batch& bt, int op, const double* part, int wstride, KScal* sc, RedBuf& rb, double* chunks,
+                 cudaStream_t st) {
+    rb.ensure(0, bt.nsys(), st);
+    const int nch = hop_red_chunks(wstride);
+    const dim3 grid(nch, bt.nsys());
+    unsigned* tk = rb.tickets.as<unsigned>();
+    ProfScope prof(PROF_BLAS, (double)bt.nsys() * wstride * 3 * sizeof(double), st);
+    if (op == B_ALPHA) k_hop_red_fin<B_ALPHA><<<grid, RF_B, 0, st>>>(bt.dev(), sc, part, wstride, chunks, nch, tk);
+    else if (op == B_OMEGA) k_hop_red_fin<B_OMEGA><<<grid, RF_B, 0, st>>>(bt.dev(), sc, part, wstride, chunks, nch, tk);
+    else throw Error(BPP_ERR_INVALID_ARG, "fused hop reductions finalize alpha or omega");
+    count_launch();
+    BPP_CHECK_LAUNCH();
+}
+
 // ----------------------------------------------------------------------------- outer loop
 struct OuterParams {
     const SysDesc* s64;

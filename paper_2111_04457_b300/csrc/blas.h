@@ -66,6 +66,14 @@ struct BlasVecs {
 void blas(const Batch& bt, int op, const BlasVecs& vv, KScal* sc, RedBuf& rb, cudaStream_t st,
           double* red_out = nullptr);
 void blas_fin(int op, KScal* sc, const double* tot, int n, cudaStream_t st);
+// B_ALPHA or B_OMEGA from the per-warp partials of a hop with fused inner
+// products (HopRed; part [system][wstride][4]): the (Vh + 31) / 32 partials of
+// each active system are summed in fixed chunks (chunk sums in `chunks`,
+// [system][hop_red_chunks(wstride)][4] doubles), then in chunk order, and
+// alpha or omega is derived; rb's tickets find the last chunk.
+int hop_red_chunks(int wstride);
+void hop_red_fin(const Batch& bt, int op, const double* part, int wstride, KScal* sc, RedBuf& rb, double* chunks,
+                 cudaStream_t st);
 
 // Outer defect-correction steps (FP64 batch b64 and inner-precision batch bP
 // over the same systems):

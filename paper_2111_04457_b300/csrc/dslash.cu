@@ -23,6 +23,7 @@
 #include "gauge.h"
 #include "hop_dev.h"
 #include "kernels.h"
+#include "reduce.h"
 
 namespace bpp {
 
@@ -425,6 +426,53 @@ __device__ __forceinline__ void hop_halo_bwd(cx<typename PT<P>::real> acc[12], c
     reconstruct<3, SB>(acc, g);
 }
 
+// The values a later kernel reads back after store_spinor (FP16: the
+// per-site scale and the half rounding; the other formats store exactly).
+template <int P>
+__device__ __forceinline__ void as_stored(cx<typename PT<P>::real> v[12]) {}
+template <>
+__device__ __forceinline__ void as_stored<P16>(cx<float> v[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].r), fabsf(v[k].i)));
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const float2 h = h2f(f2h(v[k].r * inv, v[k].i * inv));
+        v[k] = mkc(h.x * m, h.y * m);
+    }
+}
+
+// Fused BiCGStab inner products of the stored output (see HopRed): one FP64
+// partial per warp of 32 consecutive sites of system s; lanes without a
+// valid site add zero.
+template <int P>
+__device__ __forceinline__ void hop_reduce(const HopParams& hp, const SysDesc& d, int s, int it, bool valid,
+                                           cx<typename PT<P>::real> v[12], const cx<typename PT<P>::real> y[12]) {
+    using real = typename PT<P>::real;
+    as_stored<P>(v);
+    real t[3] = {0, 0, 0};
+    if (hp.red_op == HRED_ALPHA) {
+        cx<real> rh[12];
+        Access<P>::load_spinor(sys_view<P>(const_cast<char*>(hp.red_rhat), d), valid ? it : d.g.Vh - 1, rh);
+        dot12(rh, v, t[0], t[1]);
+    } else {
+        dot12(v, y, t[0], t[1]);
+        t[2] = norm12(v);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        real a = valid ? t[k] : (real)0;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        t[k] = a;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        double* o = hp.red_part + ((size_t)s * hp.red_wstride + (it >> 5)) * 4;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o[k] = (double)t[k];
+    }
+}
+
 template <int P, bool DAG, int MODE, bool DD = false, bool C = false>
 __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::value) k_hop(HopParams hp) {
     using real = typename PT<P>::real;
@@ -433,8 +481,13 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     if (hp.done && hp.done[s * hp.done_stride]) return;
     const SysDesc& d = hp.sys[s];
     const Geom g = d.g;
-    const int i = tile * blockDim.x + threadIdx.x;
-    if (i >= g.Vh) return;
+    const int it = tile * blockDim.x + threadIdx.x;
+    // a reducing launch keeps every lane of a warp that holds a valid site
+    // (the warp sums need all 32 lanes); the extra lanes redo site Vh - 1 and
+    // store nothing
+    const bool valid = it < g.Vh;
+    if (!valid && (hp.red_op == HRED_NONE || (it & ~31) >= g.Vh)) return;
+    const int i = valid ? it : g.Vh - 1;
     const int p = hp.parity, q = 1 - p;
 
     const int x1h = i % g.Lh;
@@ -526,9 +579,8 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
 
     // v = a hop (+ y, or + A y): the xpay forms as one fused multiply-add
     const real a = (real)(hp.a_sign * d.kappa);
-    cx<real> v[12];
+    cx<real> v[12], y[12];
     if (MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY || MODE == HOP_INV_XPAY) {
-        cx<real> y[12];
         Access<P>::load_spinor(sys_view<P>(hp.y, d), i, y);
         if (MODE == HOP_CLOV_XPAY) {
             cx<real> ay[12];
@@ -549,7 +601,9 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = w[k];
     }
-    Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
+    if (valid) Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
+    if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S)
+        if (hp.red_op != HRED_NONE) hop_reduce<P>(hp, d, s, it, valid, v, y);
 }
 
 // R right-hand sides of one gauge field per thread: each link is loaded once
@@ -569,8 +623,10 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
     }
     const SysDesc& d0 = hp.sys[s0];
     const Geom g = d0.g;
-    const int i = tile * blockDim.x + threadIdx.x;
-    if (i >= g.Vh) return;
+    const int it = tile * blockDim.x + threadIdx.x;
+    const bool valid = it < g.Vh;   // as in k_hop
+    if (!valid && (hp.red_op == HRED_NONE || (it & ~31) >= g.Vh)) return;
+    const int i = valid ? it : g.Vh - 1;
     const int p = hp.parity, q = 1 - p;
     const int x1h = i % g.Lh;
     const int row = i / g.Lh;
@@ -628,9 +684,8 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
     for (int r = 0; r < R; ++r) {
         const SysDesc& d = hp.sys[s0 + r];
         const real a = (real)(hp.a_sign * d.kappa);
-        cx<real> v[12];
+        cx<real> v[12], y[12];
         if (MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY || MODE == HOP_INV_XPAY) {
-            cx<real> y[12];
             Access<P>::load_spinor(sys_view<P>(hp.y, d), i, y);
             if (MODE == HOP_CLOV_XPAY) {
                 cx<real> ay[12];
@@ -651,7 +706,9 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) v[k] = w[k];
         }
-        Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
+        if (valid) Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
+        if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S)
+            if (hp.red_op != HRED_NONE) hop_reduce<P>(hp, d, s0 + r, it, valid, v, y);
     }
 }
 
@@ -668,8 +725,21 @@ double hop_bytes_per_site(int prec, int mode) {
 
 template <int P, bool DAG, int MODE>
 static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* out, char* y, cudaStream_t st,
-                     const int* done, int done_stride, const HopDD* dd = nullptr) {
+                     const int* done, int done_stride, const HopDD* dd = nullptr, const HopRed* red = nullptr) {
     HopParams hp;
+    if (red && red->op != HRED_NONE) {
+        if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S) {
+            BPP_REQUIRE(!dd && red->part && red->wstride >= (b.Vh_max + 31) / 32 &&
+                            (red->op != HRED_ALPHA || red->rhat),
+                        BPP_ERR_INVALID_ARG, "fused inner products: bad arguments");
+            hp.red_op = red->op;
+            hp.red_rhat = red->rhat;
+            hp.red_part = red->part;
+            hp.red_wstride = red->wstride;
+        } else {
+            throw Error(BPP_ERR_INVALID_ARG, "fused inner products need an FP64 / FP32 / FP16 XPAY or CLOV_XPAY hop");
+        }
+    }
     hp.halo_fwd = dd ? dd->fwd : nullptr;
     hp.halo_bwd = dd ? dd->bwd : nullptr;
     hp.halo_fwd_scale = dd ? dd->fwd_scale : nullptr;
@@ -685,6 +755,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     hp.y = y;
     hp.a_sign = a_sign;
     const std::string key = "hop" + std::to_string(P) + (DAG ? "d" : "n") + std::to_string(MODE) + (dd ? "dd" : "") +
+                            (hp.red_op ? "r" + std::to_string(hp.red_op) : "") +
                             (b.comp ? "c" : "") +
                             "_" + std::to_string(b.Vh_max) + "x" + std::to_string(b.nsys()) + (b.uniform ? "u" : "r");
     const bool may_tune = out != y && out != in;
@@ -772,7 +843,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
         bool first = true;
         for (int r = 0; r < s; ++r)
             if (b.sys[r].U[0][0].data == b.sys[s].U[0][0].data) first = false;
-        per_sys[s] = b.sys[s].g.Vh * (first ? bps : bps - lbytes);
+        per_sys[s] = b.sys[s].g.Vh * ((first ? bps : bps - lbytes) + (hp.red_op == HRED_ALPHA ? spinor_bytes(P) : 0));
         sites += b.sys[s].g.Vh;
         bytes += per_sys[s];
     }
@@ -791,39 +862,39 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
 
 template <int P, bool DAG>
 static void launch_mode(const Batch& b, int parity, int mode, double a_sign, char* in, char* out, char* y,
-                        cudaStream_t st, const int* dn, int ds, const HopDD* dd) {
+                        cudaStream_t st, const int* dn, int ds, const HopDD* dd, const HopRed* red = nullptr) {
     switch (mode) {
-        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
-        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
-        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
-        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
-        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd); break;
+        case HOP_PLAIN: launch_t<P, DAG, HOP_PLAIN>(b, parity, a_sign, in, out, y, st, dn, ds, dd, red); break;
+        case HOP_XPAY: launch_t<P, DAG, HOP_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd, red); break;
+        case HOP_CLOV_XPAY: launch_t<P, DAG, HOP_CLOV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd, red); break;
+        case HOP_INV: launch_t<P, DAG, HOP_INV>(b, parity, a_sign, in, out, y, st, dn, ds, dd, red); break;
+        case HOP_INV_XPAY: launch_t<P, DAG, HOP_INV_XPAY>(b, parity, a_sign, in, out, y, st, dn, ds, dd, red); break;
         default: throw Error(BPP_ERR_INVALID_ARG, "bad hopping mode");
     }
 }
 
 static void hop_any(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
-                    cudaStream_t st, const int* dn, int ds, const HopDD* dd) {
+                    cudaStream_t st, const int* dn, int ds, const HopDD* dd, const HopRed* red = nullptr) {
     BPP_REQUIRE(in != out, BPP_ERR_INVALID_ARG, "hopping term: output aliases input");
     if (b.prec == P64) {
-        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
-            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+        dag ? launch_mode<P64, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red)
+            : launch_mode<P64, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red);
     } else if (b.prec == P32) {
-        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
-            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+        dag ? launch_mode<P32, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red)
+            : launch_mode<P32, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red);
     } else if (b.prec == P64S) {
         BPP_REQUIRE(!dd, BPP_ERR_UNSUPPORTED, "the decomposed hopping term takes FP64, FP32 or FP16");
-        dag ? launch_mode<P64S, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
-            : launch_mode<P64S, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+        dag ? launch_mode<P64S, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red)
+            : launch_mode<P64S, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red);
     } else {
-        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd)
-            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd);
+        dag ? launch_mode<P16, true>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red)
+            : launch_mode<P16, false>(b, parity, mode, a_sign, in, out, y, st, dn, ds, dd, red);
     }
 }
 
 void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
-         cudaStream_t st, const int* dn, int ds) {
-    hop_any(b, parity, dag, mode, a_sign, in, out, y, st, dn, ds, nullptr);
+         cudaStream_t st, const int* dn, int ds, const HopRed* red) {
+    hop_any(b, parity, dag, mode, a_sign, in, out, y, st, dn, ds, nullptr, red);
 }
 
 void hop_dd(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,

@@ -31,6 +31,30 @@ struct HopParams {
     const float* halo_fwd_scale;   // FP16: the upper domain's per-site spinor scales [system][face site]
     int64_t face;                  // face sites of one parity: L1/2 L2 L3
     int flip_top, flip_bot;        // the boundary sign applies at the top / bottom face
+    // BiCGStab inner products fused into an XPAY / CLOV_XPAY epilogue (see
+    // HopRed): HRED_NONE, HRED_ALPHA or HRED_OMEGA
+    int red_op = 0;
+    const char* red_rhat = nullptr;   // HRED_ALPHA: rhat, a batch vector on the output parity
+    double* red_part = nullptr;       // per-warp partial sums [system][red_wstride][4]
+    int red_wstride = 0;              // warps per system in red_part: (Vh_max + 31) / 32
+};
+
+// Inner products of the BiCGStab iteration computed by the second hop of a
+// Schur application from the values it stores (FP16: as they will read back):
+//   HRED_ALPHA  <rhat, out>               (out = v = Mhat p)
+//   HRED_OMEGA  <out, y>, ||out||^2       (out = t = Mhat s, y = s)
+// Each warp of 32 consecutive sites of one system sums its sites in the
+// arithmetic type of the precision and writes one FP64 partial; hop_red_fin
+// then sums a system's partials in warp order.  The order of the sums depends
+// only on the lattice, not on the hopping kernel's block size or the number
+// of right-hand sides per thread, so batched and single solves stay
+// bit-identical.
+enum HopRedOp { HRED_NONE = 0, HRED_ALPHA = 1, HRED_OMEGA = 2 };
+struct HopRed {
+    int op = HRED_NONE;
+    const char* rhat = nullptr;
+    double* part = nullptr;
+    int wstride = 0;
 };
 
 // Face buffers and boundary signs of one domain of a decomposition in x4.
@@ -44,7 +68,7 @@ struct HopDD {
 
 // out_p = epilogue(a * hop_{p,1-p} in) over every system of the batch.
 void hop(const Batch& b, int parity, int dag, int mode, double a_sign, char* in, char* out, char* y,
-         cudaStream_t st, const int* done = nullptr, int done_stride = 0);
+         cudaStream_t st, const int* done = nullptr, int done_stride = 0, const HopRed* red = nullptr);
 double hop_bytes_per_site(int prec, int mode);
 // The hopping term on one domain of a decomposition in x4 (FP64 / FP32 /
 // FP16): as hop(), with the t-direction neighbour terms of the face sites

@@ -16,6 +16,7 @@
 // batch of systems (right-hand sides and/or lattices) that every launch covers;
 // the host only reads the per-system scalars every check_every iterations.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <memory>
@@ -89,6 +90,8 @@ struct Plan {
     Vec be_s, bo_s, bhat_s, xe_s, m_s, tmpo_s, r_s;
     Vec w[9];
     RedBuf rb;
+    DevBuf hred;                         // per-warp partials of the fused BiCGStab inner products
+    int hred_wstride = 0;                // 0: inner products in separate vector kernels
     DevBuf d64, dP, dloops, dod, doc;
     std::vector<KScal> h64, hP;
     bool warmed = false;                 // one eager inner solve ran (autotuner populated)
@@ -116,6 +119,14 @@ struct Plan {
         if (wgraph) cudaGraphDestroy(wgraph);
     }
 };
+
+// The BiCGStab inner products fused into the hopping kernels (default), or
+// in separate vector kernels with BPP_FUSED_DOTS=0; both are deterministic,
+// with sums grouped differently.
+static bool fused_dots() {
+    const char* e = std::getenv("BPP_FUSED_DOTS");
+    return !(e && e[0] == '0');
+}
 
 static std::mutex g_plan_mu;
 static std::vector<std::unique_ptr<Plan>> g_plans;
@@ -188,6 +199,12 @@ static Plan& get_plan(const std::vector<const Gauge*>& G, const std::vector<doub
     for (auto& v : pl->w) alloc_vec(*pl, v, pl->bP);
     const int n = (int)G.size();
     pl->rb.persistent = true;
+    if (solver == BPP_BICGSTAB && fused_dots()) {
+        pl->hred_wstride = (pl->bP.Vh_max + 31) / 32;
+        const size_t hb = (size_t)n * (pl->hred_wstride + hop_red_chunks(pl->hred_wstride)) * 4 * sizeof(double);
+        pl->hred.alloc_persistent(hb);
+        pl->bytes += hb;
+    }
     pl->d64.alloc_persistent(n * sizeof(KScal));
     pl->dP.alloc_persistent(n * sizeof(KScal));
     pl->dloops.alloc_persistent(2 * sizeof(int));
@@ -226,11 +243,30 @@ static void inner_iteration(Plan& pl, const BlasVecs& v, char* tmp, cudaStream_t
     KScal* sc = pl.dP.as<KScal>();
     const int* done = &sc[0].done;
     const int ds = (int)(sizeof(KScal) / sizeof(int));
-    auto schur_s = [&](int dag, char* in, char* out) {
+    auto schur_s = [&](int dag, char* in, char* out, const HopRed* red = nullptr) {
         hop(bP, 1, dag, pl.clover ? HOP_INV : HOP_PLAIN, -1.0, in, tmp, nullptr, st, done, ds);
-        hop(bP, 0, dag, pl.clover ? HOP_CLOV_XPAY : HOP_XPAY, +1.0, tmp, out, in, st, done, ds);
+        hop(bP, 0, dag, pl.clover ? HOP_CLOV_XPAY : HOP_XPAY, +1.0, tmp, out, in, st, done, ds, red);
     };
-    if (pl.solver == BPP_BICGSTAB) {
+    if (pl.solver == BPP_BICGSTAB && pl.hred_wstride > 0) {
+        // <rhat, v> and <t, s>, ||t||^2 come from the second hop of each Schur
+        // application (it holds v or t in registers and reads s as its xpay
+        // operand): 15 vector passes per iteration instead of 18
+        HopRed red;
+        red.part = pl.hred.as<double>();
+        red.wstride = pl.hred_wstride;
+        red.op = HRED_ALPHA;
+        red.rhat = v.rhat;
+        double* chunks = red.part + (size_t)bP.nsys() * red.wstride * 4;
+        schur_s(0, v.p, v.v, &red);
+        hop_red_fin(bP, B_ALPHA, red.part, red.wstride, sc, pl.rb, chunks, st);
+        blas(bP, B_S, v, sc, pl.rb, st);
+        red.op = HRED_OMEGA;
+        red.rhat = nullptr;
+        schur_s(0, v.s, v.t, &red);
+        hop_red_fin(bP, B_OMEGA, red.part, red.wstride, sc, pl.rb, chunks, st);
+        blas(bP, B_XR, v, sc, pl.rb, st);
+        blas(bP, B_P, v, sc, pl.rb, st);
+    } else if (pl.solver == BPP_BICGSTAB) {
         schur_s(0, v.p, v.v);
         blas(bP, B_ALPHA, v, sc, pl.rb, st);
         blas(bP, B_S, v, sc, pl.rb, st);
@@ -271,7 +307,8 @@ static void inner_init(Plan& pl, const BlasVecs& v, char* tmp, cudaStream_t st) 
 }
 
 static int body_kernel_count(const Plan& pl) {
-    // hop launches + blas launches per iteration (+ the loop control kernel)
+    // hop launches + blas launches per iteration (+ the loop control kernel);
+    // the fused BiCGStab form replaces two vector kernels by two finalize kernels
     return pl.solver == BPP_BICGSTAB ? 4 + 5 + 1 : 4 + 4 + 1;
 }
 
