@@ -436,6 +436,10 @@ void hop_red_fin(const Batch& bt, int op, const double* part, int wstride, KScal
 }
 
 // ----------------------------------------------------------------------------- outer loop
+// Compiler barrier: the loads issued before it stay ahead of the stores that
+// follow, so a thread has all of them in flight at once.
+__device__ __forceinline__ void loads_issued() { asm volatile("" ::: "memory"); }
+
 struct OuterParams {
     const SysDesc* s64;
     const SysDesc* sP;
@@ -509,11 +513,9 @@ __global__ void __launch_bounds__(BLAS_B) k_outer_down(OuterParams op) {
 __device__ __forceinline__ df64 to_df(float v) { return df64(v, 0.f); }
 __device__ __forceinline__ df64 to_df(double v) { return df64(v); }
 
-template <int P> struct OuterAccMinBlocks { static constexpr int value = 4; };
-template <> struct OuterAccMinBlocks<P64> { static constexpr int value = 2; };
 
 template <int P>
-__global__ void __launch_bounds__(BLAS_B, OuterAccMinBlocks<P>::value) k_outer_acc(OuterParams op) {
+__global__ void __launch_bounds__(BLAS_B, 2) k_outer_acc(OuterParams op) {
     using real = typename PT<P>::real;
     int s, tile;
     map_block(op.map, s, tile);
@@ -523,27 +525,42 @@ __global__ void __launch_bounds__(BLAS_B, OuterAccMinBlocks<P>::value) k_outer_a
     const double sc = op.sc[s].scale;
     cx<real> e[12];
     Access<P>::load_spinor(sys_view<P>(op.b, op.sP[s]), i, e);
-    // component by component (no whole FP64 or split spinor held in registers)
     double2* xp = op.a ? reinterpret_cast<double2*>(op.a + d.vec_off) : nullptr;
     float4* xsp = op.c ? reinterpret_cast<float4*>(op.c + d.vec_off) : nullptr;
     const df64 scd(sc);
+    // half a spinor of x at a time: its loads are issued together (the
+    // compiler barrier keeps them ahead of the stores, which it cannot prove
+    // independent of them), without holding a whole FP64 or split spinor
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const int64_t j = k * d.stride + i;
-        if (xp) {
-            double2 xv = xp[j];
-            xv.x = fma(sc, (double)e[k].r, xv.x);
-            xv.y = fma(sc, (double)e[k].i, xv.y);
-            xp[j] = xv;
+    for (int h = 0; h < 2; ++h) {
+        double2 xv[6];
+        float4 xs[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int64_t j = (6 * h + k) * d.stride + i;
+            if (xp) xv[k] = xp[j];
+            if (xsp) xs[k] = xsp[j];
         }
-        if (xsp) {
-            // the split copy takes the same update in double-float arithmetic
-            // (no FP64 conversions); beside an FP64 x it tracks x to ~1e-14 and
-            // only feeds the defects, without one (x64 null) it is the iterate
-            const float4 v = xsp[j];
-            const df64 r = normalized(fma(scd, to_df(e[k].r), df64(v.x, v.y)));
-            const df64 m = normalized(fma(scd, to_df(e[k].i), df64(v.z, v.w)));
-            xsp[j] = make_float4(r.hi, r.lo, m.hi, m.lo);
+        loads_issued();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int64_t j = (6 * h + k) * d.stride + i;
+            const cx<real> ek = e[6 * h + k];
+            if (xp) {
+                double2 xk = xv[k];
+                xk.x = fma(sc, (double)ek.r, xk.x);
+                xk.y = fma(sc, (double)ek.i, xk.y);
+                xp[j] = xk;
+            }
+            if (xsp) {
+                // the split copy takes the same update in double-float arithmetic
+                // (no FP64 conversions); beside an FP64 x it tracks x to ~1e-14 and
+                // only feeds the defects, without one (x64 null) it is the iterate
+                const float4 v = xs[k];
+                const df64 r = normalized(fma(scd, to_df(ek.r), df64(v.x, v.y)));
+                const df64 m = normalized(fma(scd, to_df(ek.i), df64(v.z, v.w)));
+                xsp[j] = make_float4(r.hi, r.lo, m.hi, m.lo);
+            }
         }
     }
 }
@@ -560,26 +577,35 @@ __global__ void __launch_bounds__(BLAS_B) k_split_residual(OuterParams op) {
     const int i = tile * blockDim.x + threadIdx.x;
     float red[4] = {0.f, 0.f, 0.f, 0.f};
     if (i < d.g.Vh) {
-        // component by component (no whole split spinor held in registers)
+        // half a spinor at a time, its loads issued together (no whole split
+        // spinor held in registers)
         const float4* pa = reinterpret_cast<const float4*>(op.a + d.vec_off);
         const float4* pb = op.b ? reinterpret_cast<const float4*>(op.b + d.vec_off) : nullptr;
         float4* pc = reinterpret_cast<float4*>(op.c + d.vec_off);
         float n = 0.f;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const int64_t j = k * d.stride + i;
-            const float4 va = pa[j];
-            df64 r(va.x, va.y), m(va.z, va.w);
-            if (pb) {
-                const float4 vb = pb[j];
-                r = r - df64(vb.x, vb.y);
-                m = m - df64(vb.z, vb.w);
+        for (int h = 0; h < 2; ++h) {
+            float4 va[6], vb[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int64_t j = (6 * h + k) * d.stride + i;
+                va[k] = pa[j];
+                if (pb) vb[k] = pb[j];
             }
-            r = normalized(r);
-            m = normalized(m);
-            pc[j] = make_float4(r.hi, r.lo, m.hi, m.lo);
-            n = fmaf(r.hi, r.hi, n);
-            n = fmaf(m.hi, m.hi, n);
+            loads_issued();
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                df64 r(va[k].x, va[k].y), m(va[k].z, va[k].w);
+                if (pb) {
+                    r = r - df64(vb[k].x, vb[k].y);
+                    m = m - df64(vb[k].z, vb[k].w);
+                }
+                r = normalized(r);
+                m = normalized(m);
+                pc[(6 * h + k) * d.stride + i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+                n = fmaf(r.hi, r.hi, n);
+                n = fmaf(m.hi, m.hi, n);
+            }
         }
         red[0] = n;
     }
@@ -638,19 +664,27 @@ __global__ void __launch_bounds__(BLAS_B) k_defect_update(OuterParams op) {
     const df64 sc = df64(-op.sc[s].scale);
     float red[4] = {0.f, 0.f, 0.f, 0.f};
     if (i < d.g.Vh) {
-        cx<df64> r[12];
         cx<float> m[12];
-        Access<P64S>::load_spinor(sys_view<P64S>(op.a, d), i, r);
         Access<P32>::load_spinor(sys_view<P32>(op.b, op.sP[s]), i, m);
+        float4* pr = reinterpret_cast<float4*>(op.a + d.vec_off);
         float n = 0.f;
+        // half a spinor of r at a time, its loads issued together with m's
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            r[k].r = fma(sc, df64(m[k].r, 0.f), r[k].r);
-            r[k].i = fma(sc, df64(m[k].i, 0.f), r[k].i);
-            n = fmaf(r[k].r.hi, r[k].r.hi, n);
-            n = fmaf(r[k].i.hi, r[k].i.hi, n);
+        for (int h = 0; h < 2; ++h) {
+            float4 rv[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rv[k] = pr[(6 * h + k) * d.stride + i];
+            loads_issued();
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const cx<float> mk = m[6 * h + k];
+                const df64 r = normalized(fma(sc, df64(mk.r, 0.f), df64(rv[k].x, rv[k].y)));
+                const df64 q = normalized(fma(sc, df64(mk.i, 0.f), df64(rv[k].z, rv[k].w)));
+                pr[(6 * h + k) * d.stride + i] = make_float4(r.hi, r.lo, q.hi, q.lo);
+                n = fmaf(r.hi, r.hi, n);
+                n = fmaf(q.hi, q.hi, n);
+            }
         }
-        Access<P64S>::store_spinor(sys_view<P64S>(op.a, d), i, r);
         red[0] = n;
     }
     double tot[4];

@@ -28,20 +28,28 @@ template <> __device__ __forceinline__ float2 to_canon<float2, df64>(cx<df64> v)
     return make_float2((float)v.r.to_double(), (float)v.i.to_double());
 }
 
-// Thread per (half-lattice site, parity) of system sys0 + blockIdx.y.
+// Parity of lexicographic site lex; its half-lattice index is lex / 2.
+__device__ __forceinline__ int lex_parity(const Geom& g, int64_t lex) {
+    const int x0 = (int)(lex % g.L[0]);
+    int r = (int)(lex / g.L[0]);
+    const int x1 = r % g.L[1];
+    r /= g.L[1];
+    return (x0 + x1 + r % g.L[2] + r / g.L[2]) & 1;
+}
+
+// Thread per lexicographic site of system sys0 + blockIdx.y: a warp reads 32
+// consecutive canonical sites (both parities), so every line of the canonical
+// field is read once.
 template <int P, class TC>
 __global__ void k_full_to_eo(const SysDesc* sys, int sys0, const TC* __restrict__ canon, int64_t cstride,
                              char* even, char* odd, int g5) {
     using real = typename PT<P>::real;
     const SysDesc& d = sys[sys0 + blockIdx.y];
     const Geom g = d.g;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * (int64_t)g.Vh) return;
-    const int p = (int)(t / g.Vh);
-    const int i = (int)(t % g.Vh);
-    int x[4];
-    eo_coords(g, i, p, x);
-    const int64_t lex = 2 * (int64_t)i + (x[0] & 1);
+    const int64_t lex = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (lex >= 2 * (int64_t)g.Vh) return;
+    const int p = lex_parity(g, lex);
+    const int i = (int)(lex >> 1);
     const TC* src = canon + blockIdx.y * cstride + lex * 12;
     cx<real> v[12];
 #pragma unroll
@@ -58,13 +66,10 @@ __global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, con
     using real = typename PT<P>::real;
     const SysDesc& d = sys[sys0 + blockIdx.y];
     const Geom g = d.g;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * (int64_t)g.Vh) return;
-    const int p = (int)(t / g.Vh);
-    const int i = (int)(t % g.Vh);
-    int x[4];
-    eo_coords(g, i, p, x);
-    const int64_t lex = 2 * (int64_t)i + (x[0] & 1);
+    const int64_t lex = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // as in k_full_to_eo
+    if (lex >= 2 * (int64_t)g.Vh) return;
+    const int p = lex_parity(g, lex);
+    const int i = (int)(lex >> 1);
     cx<real> v[12];
     Access<P>::load_spinor(sys_view<P>(const_cast<char*>(p == 0 ? even : odd), d), i, v);
     TC* dst = canon + blockIdx.y * cstride + lex * 12;
