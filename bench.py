@@ -323,12 +323,14 @@ def run_ours(args, rank, world):
     # the inner-precision hopping kernel: HBM-bound; bytes = 8 links + input and
     # output spinor per site (392 B for FP16), plus the xpay operand that the
     # second hop of each Schur application reads (52 B, half of the launches)
+    # and rhat, read by the hop that also forms <rhat, v> (52 B, a quarter)
     inner_gbs = by_in / (ms_in / 1000.0) / 1e9 if ms_in > 0 else None
     roof_inner = {"bound": "hbm", "achieved": inner_gbs, "peak": peak_hbm, "unit": "GB/s",
                   "frac": (inner_gbs / peak_hbm) if inner_gbs else None, "traffic": None,
                   "kernel": "k_hop inner precision", "peak_kind": peak_kind, "launches": n_in,
                   "avg_us": 1000 * ms_in / max(n_in, 1), "share_ms": ms_in,
-                  "bytes_counted": "8 links + in + out spinor per site, + the xpay operand of the second Schur hop"}
+                  "bytes_counted": "8 links + in + out spinor per site, + the xpay operand of the second Schur hop, "
+                                   "+ rhat where that hop also forms <rhat, v>"}
     # FP64 hopping kernel: bound by the FP64 pipe; 1320 flop per output site.
     # With the double-float check the mixed solve launches none; it is then
     # timed inside one host-driven plain FP64 solve of the same system.
