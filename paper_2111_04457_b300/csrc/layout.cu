@@ -60,42 +60,59 @@ __global__ void k_full_to_eo(const SysDesc* sys, int sys0, const TC* __restrict_
     Access<P>::store_spinor(sys_view<P>(p == 0 ? even : odd, d), i, v);
 }
 
+// Threads per block of k_eo_to_full (its shared staging buffer is sized for it).
+constexpr int EO_B = 256;
+
+// Thread per lexicographic site, as k_full_to_eo.  The block's 256
+// consecutive canonical sites are one contiguous range of the output: each
+// thread puts its site in shared memory, then the block writes the range with
+// consecutive threads on consecutive 8- or 16-byte elements (whole sectors per
+// store instruction instead of 16 bytes every 192).
 template <int P, class TC>
-__global__ void k_eo_to_full(const SysDesc* sys, int sys0, const char* even, const char* odd, TC* canon,
-                             int64_t cstride, int g5, double scale) {
+__global__ void __launch_bounds__(EO_B) k_eo_to_full(const SysDesc* sys, int sys0, const char* even, const char* odd,
+                                                     TC* canon, int64_t cstride, int g5, double scale) {
     using real = typename PT<P>::real;
+    __shared__ TC stage[EO_B * 12];
     const SysDesc& d = sys[sys0 + blockIdx.y];
     const Geom g = d.g;
-    const int64_t lex = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // as in k_full_to_eo
-    if (lex >= 2 * (int64_t)g.Vh) return;
-    const int p = lex_parity(g, lex);
-    const int i = (int)(lex >> 1);
-    cx<real> v[12];
-    Access<P>::load_spinor(sys_view<P>(const_cast<char*>(p == 0 ? even : odd), d), i, v);
-    TC* dst = canon + blockIdx.y * cstride + lex * 12;
-    if constexpr (P == P64S) {
-        // split values convert to FP64 first and scale there: the scaled
-        // solution may lie outside the FP32 exponent range; a power-of-two
-        // scale (the solver's) is applied to the exponent, without an FP64
-        // multiply
-        int e2;
-        const bool p2 = pow2_exponent(scale, e2);
+    const int64_t V = 2 * (int64_t)g.Vh;
+    const int64_t lex0 = (int64_t)blockIdx.x * EO_B;
+    if (lex0 >= V) return;   // whole block
+    const int64_t lex = lex0 + threadIdx.x;
+    if (lex < V) {
+        const int p = lex_parity(g, lex);
+        const int i = (int)(lex >> 1);
+        cx<real> v[12];
+        Access<P>::load_spinor(sys_view<P>(const_cast<char*>(p == 0 ? even : odd), d), i, v);
+        TC* dst = stage + threadIdx.x * 12;
+        if constexpr (P == P64S) {
+            // split values convert to FP64 first and scale there: the scaled
+            // solution may lie outside the FP32 exponent range; a power-of-two
+            // scale (the solver's) is applied to the exponent, without an FP64
+            // multiply
+            int e2;
+            const bool p2 = pow2_exponent(scale, e2);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const double r = v[k].r.to_double(), m = v[k].i.to_double();
-            cx<double> w = p2 ? mkc(mul_pow2(r, e2), mul_pow2(m, e2)) : mkc(r * scale, m * scale);
-            if (g5 && k < 6) w = -w;
-            dst[k] = to_canon<TC, double>(w);
+            for (int k = 0; k < 12; ++k) {
+                const double r = v[k].r.to_double(), m = v[k].i.to_double();
+                cx<double> w = p2 ? mkc(mul_pow2(r, e2), mul_pow2(m, e2)) : mkc(r * scale, m * scale);
+                if (g5 && k < 6) w = -w;
+                dst[k] = to_canon<TC, double>(w);
+            }
+        } else {
+            if (scale != 1.0) {
+                const real f = (real)scale;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) v[k] = f * v[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>((g5 && k < 6) ? -v[k] : v[k]);
         }
-    } else {
-        if (scale != 1.0) {
-            const real f = (real)scale;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) v[k] = f * v[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 12; ++k) dst[k] = to_canon<TC, real>((g5 && k < 6) ? -v[k] : v[k]);
     }
+    __syncthreads();
+    const int n = (int)min((int64_t)EO_B, V - lex0) * 12;
+    TC* out = canon + blockIdx.y * cstride + lex0 * 12;
+    for (int j = threadIdx.x; j < n; j += EO_B) out[j] = stage[j];
 }
 
 // Half fields: canonical [nsys][Vh][4][3] with system s at offset s*Vh*12.
@@ -151,7 +168,7 @@ void full_to_eo(const Batch& b, int sys0, int nsys, const void* canon, int canon
 
 void eo_to_full(const Batch& b, int sys0, int nsys, const char* even, const char* odd, void* canon, int canon_f64,
                 int64_t cstride, int g5, cudaStream_t st, double scale) {
-    const int B = 256;
+    const int B = EO_B;
     dim3 grid((unsigned)((2 * (int64_t)b.Vh_max + B - 1) / B), nsys);
     ProfScope prof(PROF_LAYOUT, 2.0 * b.sys[sys0].g.Vh * nsys * (spinor_bytes(b.prec) + (canon_f64 ? 192 : 96)), st);
     BPP_PREC_DISPATCH(b.prec, {
