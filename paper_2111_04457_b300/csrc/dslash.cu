@@ -314,6 +314,17 @@ __device__ __forceinline__ void hop_term_d(int d, cx<real> acc[12], const RAW& r
     }
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only) and their
+// group bookkeeping: wait_group N returns once at most N of this thread's
+// most recent groups are still pending.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Loads of the next hop are issued before the current one is computed for the
 // bandwidth-bound precisions (more bytes in flight per thread); FP64 is bound
 // by the FP64 pipe and keeps its registers for arithmetic.
@@ -515,13 +526,27 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
     const int64_t fidx = DD ? (int64_t)i - (int64_t)g.Lh * g.L[1] * g.L[2] * x4 : 0;
     if constexpr (P == P64S) {
         // one copy of the double-float colour product, the directions in a
-        // loop (eight inlined copies overflow the instruction cache), and the
-        // link read row by row (U) or column by column (U^dag) as it is used
+        // loop (eight inlined copies overflow the instruction cache).  Each
+        // direction's link (9 x 16 B per site) is copied to shared memory with
+        // cp.async one direction ahead, so its loads are in flight while the
+        // previous direction is computed without holding registers; the
+        // product reads it row by row (U) or column by column (U^dag).
+        extern __shared__ float4 lsm[];   // [2 buffers][9 entries][blockDim.x]
+        const int B = blockDim.x;
         const float4* sp = static_cast<const float4*>(in.data);
+        auto stage_link = [&](int k) {
+            const LinkView U = d.U[(k & 1) ? q : p][k >> 1];
+            const float4* up = static_cast<const float4*>(U.data) + pick8(ju, k);
+            float4* dst = lsm + (k & 1) * 9 * B + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) cp_async16(dst + c * B, up + c * U.stride);
+            cp_async_commit();
+        };
+        stage_link(0);
 #pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             const bool back = k & 1;
-            const int64_t uk = pick8(ju, k);
+            if (k < 7) stage_link(k + 1);
             cx<real> h[6], gk[6];
             {
                 cx<real> psi[12];
@@ -537,14 +562,17 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
 #pragma unroll
                 for (int c = 0; c < 6; ++c) h[c] = -h[c];
             }
-            const LinkView U = d.U[back ? q : p][k >> 1];
-            const float4* up = static_cast<const float4*>(U.data);
+            // this thread's copies of direction k have landed (those of k + 1
+            // may still be in flight)
+            if (k < 7) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            const float4* ul = lsm + (k & 1) * 9 * B + threadIdx.x;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 cx<real> ur[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float4 v = __ldcs(up + (back ? 3 * c + a : 3 * a + c) * U.stride + uk);
+                    const float4 v = ul[(back ? 3 * c + a : 3 * a + c) * B];
                     ur[c] = mkc(df64(v.x, v.y), back ? df64(-v.z, -v.w) : df64(v.z, v.w));
                 }
                 df_row(ur, h, gk[a], gk[3 + a]);
@@ -762,7 +790,15 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     auto run = [&](int B) {
         int nb = 0;
         hp.map = block_map(b, B, nb);
-        if constexpr (P != P64S) {
+        if constexpr (P == P64S) {
+            // the double-float kernel stages two directions' links in shared
+            // memory (the attribute is per device, so it is set at every launch)
+            const int smem = 2 * 9 * B * (int)sizeof(float4);
+            BPP_CUDA(cudaFuncSetAttribute(k_hop<P, DAG, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          2 * 9 * HopMaxThreads<P>::value * (int)sizeof(float4)));
+            k_hop<P, DAG, MODE><<<nb, B, smem, st>>>(hp);
+            return;
+        } else {
             if (dd) {
                 k_hop<P, DAG, MODE, true><<<nb, B, 0, st>>>(hp);
                 return;
