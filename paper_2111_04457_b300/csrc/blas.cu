@@ -727,23 +727,6 @@ __global__ void __launch_bounds__(BLAS_B) k_scale_split(OuterParams op) {
     const double f = op.sc[s].scale;
     cx<double> v[12];
     Access<P64>::load_spinor(sys_view<P64>(op.a, d), i, v);
-    int e2;
-    if (pow2_exponent(f, e2)) {
-        // a power-of-two scale (the solver's normalisation of b) is exact in
-        // the exponent: integer operations only
-        if (op.b) {
-            cx<df64> w[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) w[k] = mkc(df64(v[k].r, e2), df64(v[k].i, e2));
-            Access<P64S>::store_spinor(sys_view<P64S>(op.b, d), i, w);
-        }
-        if (op.c) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) v[k] = mkc(mul_pow2(v[k].r, e2), mul_pow2(v[k].i, e2));
-            Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);
-        }
-        return;
-    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = f * v[k];
     if (op.c) Access<P64>::store_spinor(sys_view<P64>(op.a, d), i, v);

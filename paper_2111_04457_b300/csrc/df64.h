@@ -14,8 +14,6 @@
 
 #include <cuda_runtime.h>
 
-#include <cstring>
-
 namespace bpp {
 
 // The FP64 route of the split for magnitudes outside 2^-74 .. 2^100, kept
@@ -24,28 +22,6 @@ namespace bpp {
 static __device__ __noinline__ void split_rare(double v, float& hi, float& lo) {
     hi = __double2float_rn(v);
     lo = __double2float_rn(v - (double)hi);
-}
-
-// v * 2^k by an FP64 multiply (the rare route of mul_pow2)
-static __device__ __noinline__ double mul_pow2_rare(double v, int k) { return ldexp(v, k); }
-
-// v * 2^k with an integer add to the exponent field when v and the product
-// are normal FP64 numbers (exact, no FP64 instruction); otherwise the FP64
-// route.
-__device__ __forceinline__ double mul_pow2(double v, int k) {
-    const long long b = __double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0 || e == 2047 || e + k < 1 || e + k > 2046) return mul_pow2_rare(v, k);
-    return __longlong_as_double(b + ((long long)k << 52));
-}
-
-// Whether f is a positive normal power of two 2^k (k returned).
-__host__ __device__ __forceinline__ bool pow2_exponent(double f, int& k) {
-    long long b;
-    memcpy(&b, &f, sizeof(b));
-    const int e = (int)((b >> 52) & 0x7FF);
-    k = e - 1023;
-    return b > 0 && (b & 0xFFFFFFFFFFFFFLL) == 0 && e > 0 && e < 2047;
 }
 
 struct df64 {
@@ -58,17 +34,13 @@ struct df64 {
     // the remaining 29 bits rounded once to FP32, so hi + lo = v to 2^-48.
     // Zero, and magnitudes outside 2^-74 .. 2^100 (where 2^(e - 1075) would not
     // be a normal FP32 number), take the FP64 route.
-    __device__ explicit df64(double v) { split(v, 0); }
-    // The split of v * 2^k, the power of two folded into the exponent.
-    __device__ df64(double v, int k) { split(v, k); }
-    __device__ void split(double v, int k) {
+    __device__ explicit df64(double v) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        const int e0 = (int)((b >> 52) & 0x7FF);
-        const int e = e0 + k;
+        const int e = (int)((b >> 52) & 0x7FF);
         if ((b << 1) == 0ULL) {
             hi = lo = __uint_as_float((unsigned)(b >> 32));   // +-0
-        } else if (e0 == 0 || e0 == 2047 || e < 949 || e > 1023 + 100) {
-            split_rare(k ? mul_pow2_rare(v, k) : v, hi, lo);
+        } else if (e < 949 || e > 1023 + 100) {
+            split_rare(v, hi, lo);
         } else {
             const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
             hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));

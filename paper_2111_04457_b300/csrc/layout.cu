@@ -87,15 +87,10 @@ __global__ void __launch_bounds__(EO_B) k_eo_to_full(const SysDesc* sys, int sys
         TC* dst = stage + threadIdx.x * 12;
         if constexpr (P == P64S) {
             // split values convert to FP64 first and scale there: the scaled
-            // solution may lie outside the FP32 exponent range; a power-of-two
-            // scale (the solver's) is applied to the exponent, without an FP64
-            // multiply
-            int e2;
-            const bool p2 = pow2_exponent(scale, e2);
+            // solution may lie outside the FP32 exponent range
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                const double r = v[k].r.to_double(), m = v[k].i.to_double();
-                cx<double> w = p2 ? mkc(mul_pow2(r, e2), mul_pow2(m, e2)) : mkc(r * scale, m * scale);
+                cx<double> w = mkc(v[k].r.to_double() * scale, v[k].i.to_double() * scale);
                 if (g5 && k < 6) w = -w;
                 dst[k] = to_canon<TC, double>(w);
             }

@@ -511,17 +511,13 @@ int solve_batch(const std::vector<const Gauge*>& G, const std::vector<double>& k
     }
     for (int s = 0; s < n; ++s)
         BPP_REQUIRE(std::isfinite(bnorm2[s]), BPP_ERR_NONFINITE, "non-finite right-hand side");
-    // The system is linear: solve D x' = b / c and return x = c x', with c the
-    // power of two for which ||b|| / c lies in [1/2, 1).  The normalised
-    // right-hand side keeps every split-FP64 value inside the FP32 exponent
-    // range whatever the scale of b, and scaling by a power of two is exact
-    // and costs no FP64 arithmetic.
+    // The system is linear: solve D x' = b / ||b|| and return x = ||b|| x'.  The
+    // normalised right-hand side keeps every split-FP64 value inside the FP32
+    // exponent range whatever the scale of b.
     for (int s = 0; s < n; ++s) {
         if (bnorm2[s] > 0.0) {
-            int e = 0;
-            std::frexp(std::sqrt(bnorm2[s]), &e);
-            bscale[s] = std::ldexp(1.0, e);
-            bnorm2[s] = bnorm2[s] / bscale[s] / bscale[s];   // exact; no overflow of bscale^2
+            bscale[s] = std::sqrt(bnorm2[s]);
+            bnorm2[s] = 1.0;
         }
         h64[s].scale = 1.0 / bscale[s];
     }
