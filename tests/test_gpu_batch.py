@@ -102,3 +102,35 @@ def test_clover_batch_uneven():
         xs, st = bpp.solve_batch(gs, bs, kappas, TOL, bpp.solve_opts(inner_prec=inner), csw=csw)
         for i, L in enumerate(lats):
             assert oracle.true_residual(Us[i], to_np(bs[i]), to_np(xs[i]), kappas[i], L, BC, Fs[i]) <= TOL
+
+
+@pytest.mark.parametrize("L", [(2, 2, 2, 2), (6, 6, 6, 10), (8, 8, 8, 8)])
+@pytest.mark.parametrize("csw", [0.0, 1.0])
+def test_fused_inner_products_match_separate(L, csw, monkeypatch):
+    """BiCGStab's <rhat, v>, <t, s> and ||t||^2 formed by the second hop of
+    each Schur application (the default; per-warp sums, partial warps on
+    these lattices: Vh = 8, 1080, 2048) and by separate vector kernels
+    (BPP_FUSED_DOTS=0, read when a solve plan is built) group the same terms
+    differently: both solves meet the tolerance by the oracle's residual, in
+    every inner precision, and their solutions agree to the solve's accuracy."""
+    bpp = lib()
+    b_np = synth.gaussian_spinor(L, seed=2)
+    F = oracle.clover_field(synth.random_links(L, seed=1), 0.12, csw, L) if csw else None
+    xs = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("BPP_FUSED_DOTS", fused)
+        g, U = gauge(L)          # a new gauge handle: new plans under this setting
+        if csw:
+            g.clover_build(0.12, csw)
+        b = to_dev(b_np)
+        for inner in (bpp.F64, bpp.F32, bpp.F16):
+            x, st = bpp.solve(g, b, 0.12, csw, TOL, bpp.solve_opts(inner_prec=inner))
+            assert st[0]["converged"] == 1
+            xn = to_np(x)
+            res = oracle.true_residual(U, b_np, xn, 0.12, L, BC, F)
+            assert res <= TOL, (fused, inner, res)
+            xs[(fused, inner)] = xn
+        del g
+    for inner in (bpp.F64, bpp.F32, bpp.F16):
+        a, c = xs[("1", inner)], xs[("0", inner)]
+        assert np.linalg.norm(a - c) / np.linalg.norm(c) <= 1e-8, inner
