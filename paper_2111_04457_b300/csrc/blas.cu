@@ -368,12 +368,35 @@ void blas_fin(int op, KScal* sc, const double* tot, int n, cudaStream_t st) {
 
 // Sum of one system's per-warp partials of a fused hop (see hop_red_fin) in
 // two fixed levels: block c of system s sums partials [c RF_CH, (c+1) RF_CH)
-// (thread t adds t, t + RF_B, ... in order, then the warps' and the block's
-// sums in order) into a chunk sum; the last block of the system, found with a
-// ticket, adds the chunk sums in chunk order and derives alpha or omega.  The
-// grouping depends only on the lattice.
+// (thread t adds t, t + RF_B, ... in order, its loads issued together, then
+// the warps' and the block's sums in order) into a chunk sum; the last block
+// of the system, found with a ticket, sums the chunk sums the same way (thread
+// t adds chunks t, t + RF_B, ...) and derives alpha or omega.  The grouping
+// depends only on the lattice.
 constexpr int RF_B = 256;
 constexpr int RF_CH = 8 * RF_B;
+
+// Block sum of three values per thread in a fixed order (warp shuffles, then
+// the warps in order); valid in thread 0.
+__device__ __forceinline__ void rf_block_sum(double a[3], double (*sh)[3]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double b = a[k];
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+        if (lane == 0) sh[warp][k] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double b = 0.0;
+            for (int w = 0; w < RF_B / 32; ++w) b += sh[w][k];
+            a[k] = b;
+        }
+    }
+}
+
 template <int OP>
 __global__ void __launch_bounds__(RF_B) k_hop_red_fin(const SysDesc* sys, KScal* sc, const double* part, int wstride,
                                                       double* chunks, int chunk_stride, unsigned* tickets) {
@@ -385,37 +408,36 @@ __global__ void __launch_bounds__(RF_B) k_hop_red_fin(const SysDesc* sys, KScal*
     if (c >= nch) return;
     const double* p = part + (size_t)s * wstride * 4;
     double a[3] = {0.0, 0.0, 0.0};
-    const int w1 = min(nw, (c + 1) * RF_CH);
-    for (int w = c * RF_CH + threadIdx.x; w < w1; w += RF_B) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a[k] += p[4 * w + k];
+    for (int j = 0; j < RF_CH / RF_B; ++j) {
+        const int w = c * RF_CH + j * RF_B + threadIdx.x;
+        if (w < nw) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) a[k] += p[4 * w + k];
+        }
     }
     __shared__ double sh[RF_B / 32][3];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int last;
+    rf_block_sum(a, sh);
+    double* c0 = chunks + (size_t)s * chunk_stride * 4;
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        double b = a[k];
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
-        if (lane == 0) sh[warp][k] = b;
+        for (int k = 0; k < 3; ++k) c0[4 * c + k] = a[k];
+        __threadfence();
+        last = atomicAdd(&tickets[s], 1u) == (unsigned)(nch - 1);
     }
     __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[k] = 0.0;
+    for (int j = threadIdx.x; j < nch; j += RF_B)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] += __ldcg(&c0[4 * j + k]);
+    rf_block_sum(a, sh);
     if (threadIdx.x != 0) return;
-    double* cs = chunks + ((size_t)s * chunk_stride + c) * 4;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        double b = 0.0;
-        for (int w = 0; w < RF_B / 32; ++w) b += sh[w][k];
-        cs[k] = b;
-    }
-    __threadfence();
-    if (atomicAdd(&tickets[s], 1u) != (unsigned)(nch - 1)) return;
-    __threadfence();
-    double tot[4] = {0.0, 0.0, 0.0, 0.0};
-    const double* c0 = chunks + (size_t)s * chunk_stride * 4;
-    for (int j = 0; j < nch; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) tot[k] += __ldcg(&c0[4 * j + k]);
     tickets[s] = 0u;
+    double tot[4] = {a[0], a[1], a[2], 0.0};
     blas_finalize<OP>(K, tot);
 }
 
