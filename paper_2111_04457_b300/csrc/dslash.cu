@@ -437,31 +437,42 @@ __device__ __forceinline__ void hop_halo_bwd(cx<typename PT<P>::real> acc[12], c
     reconstruct<3, SB>(acc, g);
 }
 
-// The values a later kernel reads back after store_spinor (FP16: the
-// per-site scale and the half rounding; the other formats store exactly).
+// Stores v as Access<P>::store_spinor does and replaces it by the values a
+// later load returns (FP16: the half rounding and the per-site scale, from
+// the same packed words; the other formats store exactly).
 template <int P>
-__device__ __forceinline__ void as_stored(cx<typename PT<P>::real> v[12]) {}
+__device__ __forceinline__ void store_read_back(const SpinorView& f, int64_t i, cx<typename PT<P>::real> v[12]) {
+    Access<P>::store_spinor(f, i, v);
+}
 template <>
-__device__ __forceinline__ void as_stored<P16>(cx<float> v[12]) {
+__device__ __forceinline__ void store_read_back<P16>(const SpinorView& f, int64_t i, cx<float> v[12]) {
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].r), fabsf(v[k].i)));
     const float inv = m > 0.f ? 1.f / m : 0.f;
+    uint4* p = static_cast<uint4*>(f.data);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const float2 h = h2f(f2h(v[k].r * inv, v[k].i * inv));
-        v[k] = mkc(h.x * m, h.y * m);
+    for (int k = 0; k < 3; ++k) {
+        uint32_t w[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[c] = f2h(v[4 * k + c].r * inv, v[4 * k + c].i * inv);
+        p[k * f.stride + i] = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float2 h = h2f(w[c]);
+            v[4 * k + c] = mkc(h.x * m, h.y * m);
+        }
     }
+    f.scale[i] = m;
 }
 
-// Fused BiCGStab inner products of the stored output (see HopRed): one FP64
-// partial per warp of 32 consecutive sites of system s; lanes without a
-// valid site add zero.
+// Fused BiCGStab inner products of the stored output v (as read back, see
+// store_read_back; see HopRed): one FP64 partial per warp of 32 consecutive
+// sites of system s; lanes without a valid site add zero.
 template <int P>
 __device__ __forceinline__ void hop_reduce(const HopParams& hp, const SysDesc& d, int s, int it, bool valid,
-                                           cx<typename PT<P>::real> v[12], const cx<typename PT<P>::real> y[12]) {
+                                           const cx<typename PT<P>::real> v[12], const cx<typename PT<P>::real> y[12]) {
     using real = typename PT<P>::real;
-    as_stored<P>(v);
     real t[3] = {0, 0, 0};
     if (hp.red_op == HRED_ALPHA) {
         cx<real> rh[12];
@@ -629,9 +640,14 @@ __global__ void __launch_bounds__(HopMaxThreads<P>::value, HopMinBlocks<P>::valu
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = w[k];
     }
+    if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S) {
+        if (hp.red_op != HRED_NONE) {
+            if (valid) store_read_back<P>(sys_view<P>(hp.out, d), i, v);
+            hop_reduce<P>(hp, d, s, it, valid, v, y);
+            return;
+        }
+    }
     if (valid) Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
-    if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S)
-        if (hp.red_op != HRED_NONE) hop_reduce<P>(hp, d, s, it, valid, v, y);
 }
 
 // R right-hand sides of one gauge field per thread: each link is loaded once
@@ -734,9 +750,15 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) v[k] = w[k];
         }
-        if (valid) Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
-        if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S)
-            if (hp.red_op != HRED_NONE) hop_reduce<P>(hp, d, s0 + r, it, valid, v, y);
+        bool reduced = false;
+        if constexpr ((MODE == HOP_XPAY || MODE == HOP_CLOV_XPAY) && P != P64S) {
+            if (hp.red_op != HRED_NONE) {
+                if (valid) store_read_back<P>(sys_view<P>(hp.out, d), i, v);
+                hop_reduce<P>(hp, d, s0 + r, it, valid, v, y);
+                reduced = true;
+            }
+        }
+        if (!reduced && valid) Access<P>::store_spinor(sys_view<P>(hp.out, d), i, v);
     }
 }
 
