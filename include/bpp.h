@@ -234,7 +234,12 @@ typedef struct {
 
 /* Fills opts with defaults: BiCGStab, FP32 inner, inner_tol 0 (per precision),
  * max_inner 20000, max_outer 50, use_x0 0, dagger 0, check_every 4, use_graph 2,
- * outer_arith 2. */
+ * outer_arith 2.
+ * BiCGStab forms <rhat, v>, <t, s> and ||t||^2 inside the second hopping
+ * kernel of each Schur application (per-warp partial sums in a fixed order);
+ * the environment variable BPP_FUSED_DOTS=0, read when a solve plan is set
+ * up, selects separate vector kernels instead.  Both are deterministic and
+ * independent of batching; they group the sums differently. */
 void bpp_solve_opts_default(bpp_solve_opts* opts);
 
 /* Solves D x = b (or D^dag x = b) for nrhs right-hand sides sharing the gauge
