@@ -11,8 +11,8 @@ reconstruction, full-D true residual, layout conversion out.  The returned x is
 re-checked outside the timed region with the FP64 D (true_resid_fp64_recheck).
 
 value = algorithmic bytes of every hopping-kernel launch of the timed steps
-(1536 / 576 / 296 B per output site for FP64 / FP32 / FP16, the last two
-with two-row links of SU(3) fields, plus the xpay and clover operands) divided by the timed wall time: the dslash GB/s the whole
+(1536 / 768 / 392 B per output site for FP64 / FP32 / FP16, plus the xpay and
+clover operands) divided by the timed wall time: the dslash GB/s the whole
 solve sustains.  The roofline block reports the inner-precision hopping
 kernel alone (CUDA events around each launch, on its stream).
 
@@ -321,7 +321,7 @@ def run_ours(args, rank, world):
     n_in, ms_in, by_in = prof[inner]
     n64, ms64, by64 = prof[0]
     # the inner-precision hopping kernel: HBM-bound; bytes = 8 links + input and
-    # output spinor per site (296 B for FP16 with two-row links), plus the xpay operand that the
+    # output spinor per site (392 B for FP16), plus the xpay operand that the
     # second hop of each Schur application reads (52 B, half of the launches)
     # and rhat, read by the hop that also forms <rhat, v> (52 B, a quarter)
     inner_gbs = by_in / (ms_in / 1000.0) / 1e9 if ms_in > 0 else None
@@ -329,8 +329,8 @@ def run_ours(args, rank, world):
                   "frac": (inner_gbs / peak_hbm) if inner_gbs else None, "traffic": None,
                   "kernel": "k_hop inner precision", "peak_kind": peak_kind, "launches": n_in,
                   "avg_us": 1000 * ms_in / max(n_in, 1), "share_ms": ms_in,
-                  "bytes_counted": "8 links (two-row: 12 reals) + in + out spinor per site, + the xpay operand of "
-                                   "the second Schur hop, + rhat where that hop also forms <rhat, v>"}
+                  "bytes_counted": "8 links + in + out spinor per site, + the xpay operand of the second Schur hop, "
+                                   "+ rhat where that hop also forms <rhat, v>"}
     # FP64 hopping kernel: bound by the FP64 pipe; 1320 flop per output site.
     # With the double-float check the mixed solve launches none; it is then
     # timed inside one host-driven plain FP64 solve of the same system.

@@ -163,50 +163,8 @@ __device__ __forceinline__ void load_link12(const LinkView& U, int64_t ju, cx<fl
     }
     third_row(u);
 }
-// Two-row FP16 links (rows 1 and 2 as 12 halves: a uint4 plane and a uint2
-// plane).  Row 3 is rebuilt from the unscaled rows, then the neighbour's
-// spinor scale multiplies all nine entries, as in the 18-half decode.
-struct Raw16c { uint4 s[3]; float sc; uint4 u0; uint2 u1; };
-
-__device__ __forceinline__ void load_link16c(const LinkView& U, int64_t ju, uint4& u0, uint2& u1) {
-    const uint4* q = static_cast<const uint4*>(U.data);
-    u0 = __ldcs(q + ju);
-    u1 = __ldcs(reinterpret_cast<const uint2*>(q + U.stride) + ju);
-}
-__device__ __forceinline__ void load_raw(Raw16c& r, const SpinorView& in, int64_t j, const LinkView& U, int64_t ju) {
-    const uint4* p = static_cast<const uint4*>(in.data);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r.s[k] = __ldg(p + k * in.stride + j);
-    r.sc = __ldg(in.scale + j);
-    load_link16c(U, ju, r.u0, r.u1);
-}
-__device__ __forceinline__ void decode(const Raw16c& r, cx<float> psi[12], cx<float> u[9]) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float2 a = h2f(r.s[k].x), b = h2f(r.s[k].y), c = h2f(r.s[k].z), d = h2f(r.s[k].w);
-        psi[4 * k + 0] = mkc(a.x, a.y);
-        psi[4 * k + 1] = mkc(b.x, b.y);
-        psi[4 * k + 2] = mkc(c.x, c.y);
-        psi[4 * k + 3] = mkc(d.x, d.y);
-    }
-    {
-        const float2 a = h2f(r.u0.x), b = h2f(r.u0.y), c = h2f(r.u0.z), d = h2f(r.u0.w);
-        const float2 e = h2f(r.u1.x), f = h2f(r.u1.y);
-        u[0] = mkc(a.x, a.y);
-        u[1] = mkc(b.x, b.y);
-        u[2] = mkc(c.x, c.y);
-        u[3] = mkc(d.x, d.y);
-        u[4] = mkc(e.x, e.y);
-        u[5] = mkc(f.x, f.y);
-    }
-    third_row(u);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = mkc(u[k].r * r.sc, u[k].i * r.sc);
-}
-
 template <int P, bool C> struct RawSel { using type = Raw<P>; };
 template <> struct RawSel<P32, true> { using type = Raw32c; };
-template <> struct RawSel<P16, true> { using type = Raw16c; };
 
 // One hop term: decode, project with (1 + S gamma_MU), colour-multiply
 // (U or U^dag), reconstruct into acc.
@@ -733,23 +691,7 @@ __global__ void __launch_bounds__(256) k_hop_multi(HopParams hp) {
     constexpr int SF = DAG ? +1 : -1;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if constexpr (P == P16 && C) {
-            // the two-row FP16 link once, decoded per right-hand side as in
-            // the one-RHS kernel
-            Raw16c raw;
-            load_link16c(d0.U[(k & 1) ? q : p][k >> 1], ju[k], raw.u0, raw.u1);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const SpinorView in = sys_view<P>(hp.in, hp.sys[s0 + r]);
-                const uint4* sp = static_cast<const uint4*>(in.data);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) raw.s[c] = __ldg(sp + c * in.stride + jn[k]);
-                raw.sc = __ldg(in.scale + jn[k]);
-                cx<real> psi[12], u[9];
-                decode(raw, psi, u);
-                hop_term_dec_d<SF>(k, acc[r], psi, u, flip[k]);
-            }
-        } else if constexpr (P == P16) {
+        if constexpr (P == P16) {
             // the raw FP16 link once; per right-hand side the same decode as
             // the one-RHS kernel (the spinor's scale folded into the link), so
             // the two forms give identical bits
@@ -884,7 +826,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
                 return;
             }
         }
-        if constexpr (P == P32 || P == P16) {
+        if constexpr (P == P32) {
             if (b.comp) {
                 k_hop<P, DAG, MODE, false, true><<<nb, B, 0, st>>>(hp);
                 return;
@@ -903,7 +845,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
         for (int t = 0; t <= MAXSYS; ++t) m.tile_start[t] = 0;
         hp.map = m;
         const int nb = m.tiles_per_sys * m.nsys;
-        if constexpr (P == P32 || P == P16) {
+        if constexpr (P == P32) {
             if (b.comp) {
                 if (R == 2) k_hop_multi<P, DAG, MODE, 2, true><<<nb, B, 0, st>>>(hp);
                 else k_hop_multi<P, DAG, MODE, 4, true><<<nb, B, 0, st>>>(hp);
@@ -952,7 +894,7 @@ static void launch_t(const Batch& b, int parity, double a_sign, char* in, char* 
     // algorithmic bytes: systems that share a gauge field (the right-hand sides
     // of one lattice) read its links once per launch
     double sites = 0, bytes = 0;
-    const double lb = b.comp ? (P == P16 ? 24.0 : 48.0) : (double)link_bytes(P);
+    const double lb = b.comp ? 48.0 : (double)link_bytes(P);
     const double bps = hop_bytes_per_site(P, MODE) - 8.0 * (link_bytes(P) - lb), lbytes = 8.0 * lb;
     std::vector<double> per_sys(b.nsys());
     for (int s = 0; s < b.nsys(); ++s) {

@@ -101,15 +101,6 @@ template <> struct Link12Store<P32> {
             p[k * stride + i] = make_float4((float)m[2 * k].x, (float)m[2 * k].y, (float)m[2 * k + 1].x, (float)m[2 * k + 1].y);
     }
 };
-template <> struct Link12Store<P16> {
-    static __device__ void store(void* base, int64_t stride, int64_t i, const double2 m[9]) {
-        uint4* p = static_cast<uint4*>(base);
-        p[i] = make_uint4(f2h((float)m[0].x, (float)m[0].y), f2h((float)m[1].x, (float)m[1].y),
-                          f2h((float)m[2].x, (float)m[2].y), f2h((float)m[3].x, (float)m[3].y));
-        uint2* q = reinterpret_cast<uint2*>(p + stride);
-        q[i] = make_uint2(f2h((float)m[4].x, (float)m[4].y), f2h((float)m[5].x, (float)m[5].y));
-    }
-};
 template <int P>
 __global__ void k_links_in12(Geom g, const double2* __restrict__ U, void* out, int64_t stride, size_t field_bytes) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -151,15 +142,13 @@ void links_to_internal(Gauge& G, const void* U_dev, cudaStream_t s) {
     G.su3 = maxdev <= 1e-10f;
     if (!G.su3) return;
     BPP_CUDA(cudaMalloc(&G.links12[P32], 8 * link12_alloc_bytes(P32, G.stride)));
-    BPP_CUDA(cudaMalloc(&G.links12[P16], 8 * link12_alloc_bytes(P16, G.stride)));
     k_links_in12<P32><<<grid, B, 0, s>>>(G.g, static_cast<const double2*>(U_dev), G.links12[P32], G.stride, link12_alloc_bytes(P32, G.stride));
-    k_links_in12<P16><<<grid, B, 0, s>>>(G.g, static_cast<const double2*>(U_dev), G.links12[P16], G.stride, link12_alloc_bytes(P16, G.stride));
-    count_launch(2);
+    count_launch();
     BPP_CHECK_LAUNCH();
 }
 
 bool link_compression(const Gauge& G, int prec) {
-    if (!G.su3 || (prec != P32 && prec != P16) || !G.links12[prec]) return false;
+    if (!G.su3 || prec != P32 || !G.links12[prec]) return false;
     const char* e = std::getenv("BPP_LINK_COMPRESSION");
     return !(e && e[0] == '0');
 }

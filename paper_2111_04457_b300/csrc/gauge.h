@@ -10,10 +10,10 @@ struct bpp_gauge_s {
     int64_t V = 0, Vh = 0, stride = 0;
     int device = 0;
     void* links[bpp::NPREC] = {};    // per storage format: 8 link fields [parity][mu]
-    // every link is SU(3) (checked at creation): FP32 and FP16 also keep the
-    // two-row form (rows 1 and 2; row 3 = conj(row1 x row2) is rebuilt)
+    // every link is SU(3) (checked at creation): FP32 also keeps the two-row
+    // form (rows 1 and 2; row 3 = conj(row1 x row2) is rebuilt)
     bool su3 = false;
-    void* links12[bpp::NPREC] = {};  // FP32: 3 planes of float4; FP16: a uint4 and a uint2 plane
+    void* links12[bpp::NPREC] = {};  // FP32: 3 planes of float4
     bool has_clover = false;
     double clov_kappa = 0.0, clov_csw = 0.0;
     void* clover[bpp::NPREC] = {};   // per storage format: A_e, A_o, Ainv_e, Ainv_o
@@ -27,11 +27,7 @@ inline size_t clover_alloc_bytes(int prec, int64_t stride) {
     return (size_t)stride * ((prec == P64 || prec == P64S) ? 576 : prec == P32 ? 288 : 144);
 }
 
-// Two-row links: FP32 3 planes of float4 (48 B per link), FP16 one plane of
-// uint4 and one of uint2 (the 12 halves of rows 1 and 2, 24 B per link).
-inline size_t link12_alloc_bytes(int prec, int64_t stride) {
-    return (size_t)stride * (prec == P32 ? 48 : prec == P16 ? 24 : 0);
-}
+inline size_t link12_alloc_bytes(int prec, int64_t stride) { return (size_t)stride * (prec == P32 ? 48 : 0); }
 
 inline LinkView link12_view(const Gauge& G, int prec, int parity, int mu) {
     LinkView v;
